@@ -1,0 +1,384 @@
+"""Benchmark: batched range retrieval on a proximity graph, one GB300 per rank.
+
+Workload (default): 1,000,000 uint8 vectors, d=128, 1,000-centre Gaussian
+mixture with near-duplicate families; Vamana-style graph R=64, L_build=128,
+alpha=1.2 (built once, deterministic, not timed); 10,000 queries; squared-L2
+radius chosen so that ~60% of the queries match nothing.
+
+Metric: range QPS at average precision >= 0.95 (Def. 2.2).  As in the paper's
+evaluation (Sec. 5: sweep the starting beam, report the Pareto frontier), the
+starting beam b is swept per variant against exact ground truth (the library's
+exhaustive search, Def. 2.1) and the fastest (variant, b) reaching AP >= 0.95
+is the operating point.  A step is one rr_range_search over the whole batch
+(beam phase, early stop, phase 2, CSR assembly).
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Under torchrun (N > 1) every rank runs the same per-GPU batch on its own GPU
+(weak scaling); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import rrsynth  # noqa: E402
+
+CACHE = os.path.join(ROOT, "_cache")
+BEAMS = [8, 12, 16, 24, 32, 48, 64, 96, 128, 192, 256, 384, 512]
+VARIANTS = ["greedy", "greedy_es", "doubling", "doubling_es", "beam", "beam_es"]
+# Alg. 5 thresholds swept for the early-stopping variants: (vl, esr / r)
+ES_GRID = [(20, 1.0), (50, 1.5), (100, 2.0)]
+AP_TARGET = 0.95
+
+
+def log(*a):
+    print("[bench]", *a, file=sys.stderr, flush=True)
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ------------------------------------------------------------------------------------------------
+# clocks during the timed region
+# ------------------------------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(CACHE, "clocks_%d_%d.csv" % (os.getpid(), gpu_index))
+
+    def __enter__(self):
+        os.makedirs(CACHE, exist_ok=True)
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx.append(float(p[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        try:
+            os.remove(self.path)
+        except OSError:
+            pass
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------------------------------------------
+# helpers
+# ------------------------------------------------------------------------------------------------
+
+def csr_keys(offsets, ids, n):
+    """(query, id) pairs of a CSR result as sorted int64 keys q * n + id."""
+    q = np.repeat(np.arange(len(offsets) - 1, dtype=np.int64), np.diff(offsets))
+    return np.sort(q * n + ids.astype(np.int64))
+
+
+def average_precision(truth_keys, res, n):
+    """Def. 2.2: sum_q |K_q n K'_q| / sum_q |K_q|, with K and K' as (query, id) key sets."""
+    if len(truth_keys) == 0:
+        return 1.0
+    found = csr_keys(res.offsets, res.ids, n)
+    return float(np.isin(found, truth_keys, assume_unique=True).sum()) / len(truth_keys)
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        j = json.load(open(p))
+        return float(j["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def run_reference(args, cfg, ds):
+    """The oracle (plain C, Alg. 6's parallel for over host cores) on a bounded sample per step."""
+    import oracle
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    oi = oracle.Index(ds.X, ds.adj, ds.start)
+    variant, beam = args.ref_variant, args.ref_beam
+    cores = os.cpu_count() or 1
+    sample = args.ref_sample
+    Q = ds.Q[:sample]
+    for _ in range(args.warmup if args.warmup < 1 else 1):
+        oracle.range_search(oi, Q[: max(1, sample // 10)], ds.radius, variant, beam=beam, threads=cores)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.range_search(oi, Q, ds.radius, variant, beam=beam, threads=cores)
+    dt = time.perf_counter() - t0
+    qps = args.steps * sample / dt
+    line = {"metric": "range QPS at AP>=0.95", "value": qps, "unit": "queries/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1000 * dt / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": cfg.name + ": n=%d d=%d uint8, nq=%d, R=%d" % (cfg.n, cfg.d, cfg.nq, cfg.R),
+                       "variant": variant, "beam": beam},
+            "cpu_baseline": {"value": qps, "unit": "queries/s", "cores": cores, "kind": "oracle",
+                             "sample": "first %d of the %d queries per step, %s b=%d" % (sample, cfg.nq, variant, beam)},
+            "e2e": {"value": qps, "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="own", choices=["own", "reference"])
+    ap.add_argument("--config", default="c1")
+    ap.add_argument("--variants", default=",".join(VARIANTS))
+    ap.add_argument("--beams", default=",".join(map(str, BEAMS)))
+    ap.add_argument("--cpu-sample", type=int, default=0, help="queries for the cpu_baseline leg (0 = auto)")
+    ap.add_argument("--ref-variant", default="greedy_es")
+    ap.add_argument("--ref-beam", type=int, default=16)
+    ap.add_argument("--ref-sample", type=int, default=300)
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+
+    ws, rank, local = dist_env()
+    cfg = rrsynth.CONFIGS[args.config]
+    t0 = time.time()
+    ds = rrsynth.make_dataset(cfg, cache_dir=CACHE, verbose=rank == 0)
+    if rank == 0:
+        log("dataset %s ready in %.1fs (graph build %.1fs)" % (cfg.name, time.time() - t0, ds.build_s))
+    if args.impl == "reference":
+        run_reference(args, cfg, ds)
+        return
+
+    import torch
+    import paper_2502_13245_gb300 as rr
+    rr.build()
+    dev = local if ws > 1 else 0
+    torch.cuda.set_device(dev)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", dev))
+    stream = torch.cuda.Stream()
+    sh = stream.cuda_stream
+
+    gi = rr.Index.from_arrays(ds.X, ds.adj, ds.start, device=dev)
+    Qd = torch.from_numpy(ds.Q).to("cuda:%d" % dev)
+    nq = Qd.shape[0]
+
+    # ground truth: the library's exhaustive search (Def. 2.1)
+    tt = time.time()
+    gt = gi.brute_force(ds.Q, ds.radius)
+    truth = csr_keys(gt.offsets, gt.ids, ds.X.shape[0])
+    if rank == 0:
+        log("ground truth in %.1fs: %d results, zero-result fraction %.3f" % (
+            time.time() - tt, len(truth), float(np.mean(np.diff(gt.offsets) == 0))))
+
+    def params(form, beam, **kw):
+        variant, vl, esr = form
+        return rr.rr_params_init(beam=beam, es_visit_limit=vl, es_radius_mode=1, es_radius=float(ds.radius) * esr,
+                                 **kw)
+
+    def run_once(form, beam, profile=0, stats=0):
+        p = params(form, beam, profile=profile, collect_stats=stats)
+        st, res = rr.rr_range_search(gi.h, Qd, ds.radius, form[0], p, stream=sh, result_on_device=False)
+        return rr.RangeResult(res, st)
+
+    def time_form(form, beam, reps=3):
+        p = params(form, beam)
+        variant = form[0]
+        with torch.cuda.stream(stream):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for _ in range(reps):
+                st, res = rr.rr_range_search(gi.h, Qd, ds.radius, variant, p, stream=sh, result_on_device=True)
+                rr.rr_result_free(res)
+            e1.record(stream)
+            torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    # sweep (untimed for the metric): AP and a short timing per (variant, b)
+    sweep = []
+    forms = []
+    for variant in [v for v in args.variants.split(",") if v]:
+        if variant.endswith("_es"):
+            forms += [(variant, vl, esr) for vl, esr in ES_GRID]
+        else:
+            forms.append((variant, 20, 1.0))
+    for form in forms:
+        reached = 0
+        last_ap = -1.0
+        for beam in [int(b) for b in args.beams.split(",") if b]:
+            res = run_once(form, beam)
+            apv = average_precision(truth, res, ds.X.shape[0])
+            ms = time_form(form, beam, reps=2)
+            sweep.append({"variant": form[0], "es_vl": form[1], "es_r": form[2], "beam": beam, "ap": apv, "ms": ms,
+                          "qps": nq / (ms / 1000)})
+            if rank == 0:
+                log("sweep %-12s vl=%-3d esr=%.2fr b=%-4d AP=%.4f  %.3f ms  %.0f QPS" % (
+                    form[0], form[1], form[2], beam, apv, ms, nq / (ms / 1000)))
+            if apv >= AP_TARGET:
+                reached += 1
+                if reached >= 2:
+                    break  # larger beams only cost more once the target is met
+            if form[0].endswith("_es") and abs(apv - last_ap) < 1e-4 and apv < AP_TARGET and beam >= 64:
+                break  # early stop caps this form's precision: more beam does not help
+            last_ap = apv
+    ok = [s for s in sweep if s["ap"] >= AP_TARGET]
+    if not ok:
+        best = max(sweep, key=lambda s: s["ap"])
+        log("no form reached AP >= %.2f; timing the most accurate one" % AP_TARGET)
+    else:
+        best = max(ok, key=lambda s: s["qps"])
+    plain = [s for s in ok if s["variant"] == "beam"]
+    plain_best = max(plain, key=lambda s: s["qps"]) if plain else None
+    variant, beam = best["variant"], best["beam"]
+    form = (variant, best["es_vl"], best["es_r"])
+
+    # exact counters of the chosen form -> algorithmic bytes (the beam phase alone: its own variant)
+    beam_only = ("beam_es" if variant.endswith("_es") else "beam", form[1], form[2])
+    st_full = run_once(form, beam, stats=1).stats
+    st_beam = run_once(beam_only, beam, stats=1).stats
+    row = ds.X.shape[1] * ds.X.dtype.itemsize
+    R = ds.adj.shape[1]
+    bytes_beam = int(st_beam["visits_beam"].sum()) * 4 * R + int(st_beam["distinct"].sum()) * row + nq * row
+    bytes_all = (int(st_full["visits_beam"].sum()) + int(st_full["visits_phase2"].sum())) * 4 * R + \
+        int(st_full["distinct"].sum()) * row + nq * row
+
+    # timed region: K steps, inputs resident in HBM, results left on the device
+    p = params(form, beam)
+    pp = params(form, beam, profile=1)
+    for _ in range(max(3, args.warmup)):
+        st, res = rr.rr_range_search(gi.h, Qd, ds.radius, variant, p, stream=sh, result_on_device=True)
+        rr.rr_result_free(res)
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    launches = 0
+    beam_ms = []
+    with ClockSampler(dev) as clk:
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            st, res = rr.rr_range_search(gi.h, Qd, ds.radius, variant, pp, stream=sh, result_on_device=True)
+            prof = rr.rr_last_profile(gi.h)
+            launches += prof.launches
+            beam_ms.append(prof.beam_ms)
+            rr.rr_result_free(res)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    step_ms = e0.elapsed_time(e1) / args.steps
+    if ws > 1:
+        from paper_2502_13245_gb300 import multi
+        step_ms = multi.reduce_max(step_ms, device="cuda:%d" % dev)
+        torch.distributed.barrier()
+    clocks = clk.summary()
+    value = ws * nq / (step_ms / 1000.0)
+
+    # end to end through the public API with host buffers: pinned queries in, host CSR out
+    Qh = torch.from_numpy(ds.Q).pin_memory()
+    h2d = int(Qh.numel() * Qh.element_size())
+    d2h = 0
+    torch.cuda.synchronize()
+    te0 = time.perf_counter()
+    for _ in range(args.steps):
+        st, res = rr.rr_range_search(gi.h, Qh, ds.radius, variant, p, stream=sh, result_on_device=False)
+        d2h = (res.nq + 1) * 8 + res.total * 8 + res.nq
+        rr.rr_result_free(res)
+    torch.cuda.synchronize()
+    e2e_ms = 1000 * (time.perf_counter() - te0) / args.steps
+
+    hbm, peak_kind = peaks()
+    kern_ms = float(np.mean(beam_ms))
+    achieved = bytes_beam / (kern_ms / 1000.0) / 1e9
+    whole = bytes_all / (step_ms / 1000.0) / 1e9
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        import oracle
+        oi = oracle.Index(ds.X, ds.adj, ds.start)
+        cores = os.cpu_count() or 1
+        sample = args.cpu_sample or 200
+        tc = time.perf_counter()
+        oracle.range_search(oi, ds.Q[:sample], ds.radius, variant, beam=beam, threads=cores, es_vl=form[1],
+                            es_radius=float(ds.radius) * form[2])
+        dt = time.perf_counter() - tc
+        cpu = {"value": sample / dt, "unit": "queries/s", "cores": cores, "kind": "oracle",
+               "sample": "first %d of the %d queries, %s b=%d, one pass" % (sample, nq, variant, beam)}
+
+    if rank == 0:
+        line = {
+            "metric": "range QPS at AP>=0.95", "value": value, "unit": "queries/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": step_ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+            "config": {"workload": "%s: n=%d d=%d uint8 L2, nq=%d per GPU, Vamana R=%d L=%d alpha=%.2f" % (
+                cfg.name, cfg.n, cfg.d, cfg.nq, cfg.R, cfg.L_build, cfg.alpha),
+                "variant": variant, "beam": beam, "ap": best["ap"],
+                "plain_beam_form": None if plain_best is None else {
+                    "beam": plain_best["beam"], "qps": plain_best["qps"], "ap": plain_best["ap"]},
+                "l2_policy": "index (vectors + adjacency %.0f MB) larger than L2" % (
+                    (ds.X.nbytes + ds.adj.nbytes) / 1e6)},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                         "frac": achieved / hbm, "traffic": None, "kernel": "beam phase (Alg. 1 + Alg. 5)",
+                         "peak_kind": peak_kind, "whole_step_gbs": whole},
+            "e2e": {"value": ws * nq / (e2e_ms / 1000.0), "unit": "queries/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "gpu_launches": launches,
+            "clocks": clocks,
+            "cpu_baseline": cpu,
+            "sweep": [{k: (round(v, 5) if isinstance(v, float) else v) for k, v in s.items()} for s in sweep],
+        }
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,216 @@
+/*
+ * rr.h -- C ABI of librr.so: batched range retrieval on a proximity graph, on
+ * one NVIDIA GB300 (sm_103a).
+ *
+ * The method is "Range Retrieval with Graph-Based Indices" (arXiv 2502.13245):
+ *   Def. 2.1  range search: every point p with d(p, q) <= r;
+ *   Alg. 1    BeamSearch, Alg. 5 early stopping on d_visited,
+ *   Alg. 2    GreedySearch (in-radius expansion), Alg. 3 DoublingSearch,
+ *   Alg. 6    GreedyRangeSearch, the per-query driver (a parallel for over
+ *             queries; here one launch over the whole batch).
+ * Distances are squared L2 or negative inner product (Sec. 2): exact int32 for
+ * 8-bit vectors, fp32 for float vectors.  Ties are broken by (distance, id)
+ * everywhere, so on 8-bit data the results are bit-exact against a plain CPU
+ * transcription of the algorithms.
+ *
+ * Conventions for every entry point:
+ *   - the return value is an rr_status; on failure rr_last_error() returns a
+ *     message for the calling thread (valid until that thread's next call);
+ *   - no C++ exception and no device trap crosses this boundary; device-side
+ *     problems (iteration guard, result overflow) come back as statuses;
+ *   - pointers may be host or device memory where stated ("host or device":
+ *     the library asks the driver which it is);
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream); all device work of a call is ordered on it.
+ * Thread safety: calls on different rr_index handles may run concurrently;
+ * calls on the same handle must be serialised by the caller (the handle owns
+ * one scratch arena).
+ */
+#ifndef RR_H
+#define RR_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    RR_OK = 0,
+    RR_EINVAL = 1,     /* bad argument */
+    RR_ENOMEM = 2,     /* host or device allocation failed */
+    RR_ECUDA = 3,      /* a CUDA runtime call failed */
+    RR_EFORMAT = 4,    /* index file malformed or checksum mismatch */
+    RR_EOVERFLOW = 5,  /* results exceeded max_results_total (result kept, flags set) */
+    RR_ETIMEOUT = 6,   /* a device wait or host poll ran out of time */
+    RR_EBUSY = 7,      /* serving: request not finished yet, or queue full */
+    RR_EINTERNAL = 8   /* a device-side guard tripped (should not happen) */
+} rr_status;
+
+/* Search variants (Sec. 4):
+ *   RR_BEAM          Alg. 1, returns {n in B : d(n,q) <= r} (at most b results)
+ *   RR_BEAM_ES       the same with Alg. 5 early stopping
+ *   RR_DOUBLING(_ES) Alg. 3 from the start point: repeat Alg. 1 with S <- S u V,
+ *                    b <- 2b while |N| = b (lambda = 1), beam capped at b_max
+ *   RR_GREEDY(_ES)   Alg. 6: Alg. 1, then Alg. 2 seeded with N when |N| = b   */
+typedef enum {
+    RR_BEAM = 0,
+    RR_BEAM_ES = 1,
+    RR_DOUBLING = 2,
+    RR_DOUBLING_ES = 3,
+    RR_GREEDY = 4,
+    RR_GREEDY_ES = 5
+} rr_variant;
+
+typedef enum { RR_U8 = 0, RR_I8 = 1, RR_F32 = 2 } rr_dtype;
+typedef enum { RR_L2 = 0, RR_IP = 1 } rr_metric;
+
+/* Traversal precision for fp32 indexes (Sec. 5 traverses floats in 8 bits and
+ * re-ranks; here BF16 or FP8-e4m3 with a per-vector scale and FP32
+ * accumulation).  Membership is always decided by an exact fp32 recheck. */
+typedef enum { RR_PREC_EXACT = 0, RR_PREC_BF16 = 1, RR_PREC_FP8 = 2 } rr_precision;
+
+/* Per-query result flags (rr_result.flags). */
+enum {
+    RR_FLAG_TRUNCATED = 1,     /* doubling hit b_max, or results hit max_results_total */
+    RR_FLAG_EARLY_STOPPED = 2, /* Alg. 5 ended the first beam search */
+    RR_FLAG_PHASE2 = 4         /* the greedy or doubling phase ran */
+};
+
+typedef struct rr_index rr_index;
+
+typedef struct {
+    int32_t beam;              /* b, the (starting) beam width, >= 1 */
+    int32_t b_max;             /* doubling cap on b (default 32768) */
+    int32_t es_visit_limit;    /* Alg. 5 vl (default 20) */
+    int32_t es_radius_mode;    /* 0: esr = the query's radius; 1: esr = es_radius */
+    double es_radius;          /* Alg. 5 esr when es_radius_mode = 1 */
+    int32_t precision;         /* rr_precision (fp32 indexes only) */
+    float recheck_eps;         /* low-precision slack: recheck when approx <= r + eps*|r| (0 = derive) */
+    int32_t persistent;        /* 1: one persistent launch with a device work queue */
+    int32_t collect_stats;     /* 1: fill rr_result.stats (exact visit / distinct-id counts) */
+    int64_t max_results_total; /* cap on the summed result count (0 = default 1<<28) */
+    int32_t tile_hint;         /* warps per CTA for the beam kernel (0 = library choice) */
+    int32_t profile;           /* 1: record per-phase device times, see rr_last_profile */
+    int32_t reserved[6];
+} rr_params;
+
+/* Exact per-query counters (collect_stats = 1).  visits_* count |V| of the
+ * algorithms; distinct counts the distinct ids whose distance was evaluated. */
+typedef struct {
+    int32_t visits_beam;   /* summed over every BeamSearch round */
+    int32_t visits_phase2; /* GreedySearch visits (= result count when it ran) */
+    int32_t distinct;      /* distinct ids evaluated (start point included) */
+    int32_t rounds;        /* BeamSearch calls */
+    int32_t final_beam;    /* b of the last BeamSearch */
+    int32_t evals;         /* distance evaluations actually performed by the GPU */
+} rr_query_stats;
+
+/* Results as CSR: query i owns ids[offsets[i] .. offsets[i+1]) sorted by
+ * (distance, id).  dists holds int32 (integer indexes) or float32 (fp32
+ * indexes), see dist_dtype.  Allocated by the library, freed by rr_result_free. */
+typedef struct {
+    int64_t nq;
+    int64_t total;
+    int64_t *offsets;        /* nq + 1 entries */
+    uint32_t *ids;
+    void *dists;
+    int32_t dist_dtype;      /* 0 = int32, 1 = float32 */
+    int32_t on_device;       /* 1: all arrays are device memory */
+    uint8_t *flags;          /* nq entries of RR_FLAG_* */
+    rr_query_stats *stats;   /* nq entries, or NULL unless collect_stats */
+    void *_stream;           /* internal: stream the device arrays are ordered on */
+    int32_t _device;
+    int32_t _pad;
+} rr_result;
+
+/* Fill *p with the defaults: beam 64, b_max 32768, vl 20, esr = r, exact
+ * precision, no persistent kernel, no stats, max_results_total 1<<28. */
+void rr_params_init(rr_params *p);
+
+/* Build an index from arrays in host or device memory; the library copies
+ * them into device memory it owns on `device`.
+ *   vectors    n x d row-major, element type dtype
+ *   adjacency  n x R uint32 row-major; 0xFFFFFFFF pads rows of degree < R
+ *   start      entry point of every search (the medoid), 0 <= start < n
+ * Requirements: 1 <= n < 2^31, 1 <= d <= 512 (8-bit) or 128 (fp32... see
+ * rr_index_info for the accepted maximum), 1 <= R <= 128, every non-padding
+ * adjacency entry < n.  Adjacency entries are not validated on the device;
+ * invalid ids give RR_EINVAL when validate != 0 (a host-side scan). */
+rr_status rr_create_index(const void *vectors, int64_t n, int32_t d, int32_t dtype, int32_t metric,
+                          const uint32_t *adjacency, int32_t R, int64_t start, int32_t device,
+                          int32_t validate, rr_index **out);
+
+/* Load an index file (.rrx, little endian): a 64-byte header
+ *   'RRX1', u32 version 1, i64 n, i32 d, i32 dtype, i32 metric, i32 R,
+ *   i64 start, u64 checksum, 16 zero bytes
+ * then the vectors (n*d elements) and the adjacency (n*R uint32).  The
+ * checksum is XOR over the payload's little-endian u64 words w_i (zero padded)
+ * of (w_i * 0x100000001B3 + i).  Errors: RR_EFORMAT (bad header, size or
+ * checksum), RR_EINVAL (bad values), RR_ENOMEM, RR_ECUDA. */
+rr_status rr_load_index(const char *path, int32_t device, rr_index **out);
+
+rr_status rr_free_index(rr_index *index);
+
+typedef struct {
+    int64_t n;
+    int32_t d;
+    int32_t dtype;
+    int32_t metric;
+    int32_t R;
+    int64_t start;
+    int64_t device_bytes;  /* HBM held by the index (vectors, low-precision copies, adjacency) */
+    int32_t row_stride;    /* bytes per stored vector (16-byte aligned) */
+    int32_t device;
+} rr_index_info;
+
+rr_status rr_index_info_get(const rr_index *index, rr_index_info *info);
+
+/* Batched range search (Alg. 6 / Alg. 3 / plain beam search over a batch).
+ *   queries    nq x d, the index's element type, host or device memory
+ *   radii      nq radii (host memory), or NULL to use `radius` for every query;
+ *              in the metric's own units (squared L2, or negative inner product)
+ *   variant    rr_variant; params may be NULL (defaults)
+ *   result_on_device  1: result arrays in device memory (ordered on stream),
+ *              0: host memory
+ * Returns once the result sizes are known (one host synchronisation per
+ * phase); the CSR is complete when the call returns for host results, and
+ * when `stream` reaches this point for device results.  RR_EOVERFLOW keeps a
+ * valid, truncated result with RR_FLAG_TRUNCATED set on the affected queries. */
+rr_status rr_range_search(rr_index *index, const void *queries, int64_t nq, const double *radii, double radius,
+                          int32_t variant, const rr_params *params, void *stream, int32_t result_on_device,
+                          rr_result *out);
+
+/* Exact range search by exhaustive scan (Def. 2.1), the ground truth for
+ * average precision (Def. 2.2).  Same argument conventions as
+ * rr_range_search; 8-bit indexes use exact integer arithmetic. */
+rr_status rr_brute_force(rr_index *index, const void *queries, int64_t nq, const double *radii, double radius,
+                         void *stream, int32_t result_on_device, rr_result *out);
+
+/* Per-phase device times of the last rr_range_search on an index that ran
+ * with params.profile = 1 (CUDA events on the call's stream), and the number
+ * of kernels the call launched.  Waits for the call's last event. */
+typedef struct {
+    float beam_ms;        /* beam phase: Alg. 1 (+ Alg. 5), range filter, phase-2 queue */
+    float phase2_ms;      /* Alg. 2 levels or Alg. 3 rounds (0 if none ran) */
+    float output_ms;      /* scan, copy / scatter, per-query sort */
+    float total_ms;       /* first to last event of the call */
+    int32_t launches;     /* kernels launched by the call */
+    int32_t phase2_steps; /* greedy levels or doubling rounds */
+    int32_t phase2_queries;
+    int32_t valid;        /* 1 if the last call on this index was profiled */
+} rr_profile;
+
+rr_status rr_last_profile(rr_index *index, rr_profile *out);
+
+/* Free the arrays of a result (host or device) and zero the struct. */
+rr_status rr_result_free(rr_result *result);
+
+/* Message of the calling thread's last failure ("" if none). */
+const char *rr_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RR_H */

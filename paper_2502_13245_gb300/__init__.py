@@ -1,0 +1,319 @@
+"""GB300-native batched range retrieval on a proximity graph.
+
+Python binding of ``librr.so`` (C ABI in ``include/rr.h``): argument
+marshalling only, every step of the search runs in the library's CUDA
+kernels.  The functions named ``rr_*`` mirror the C entry points one to one;
+``Index`` is a small convenience wrapper over them.
+
+Method: "Range Retrieval with Graph-Based Indices" (arXiv 2502.13245) --
+Alg. 1 BeamSearch, Alg. 5 early stopping, Alg. 2 GreedySearch, Alg. 3
+DoublingSearch and the Alg. 6 driver, over a Vamana-style graph.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from ._build import LIB, build  # noqa: F401
+
+RR_OK, RR_EINVAL, RR_ENOMEM, RR_ECUDA, RR_EFORMAT, RR_EOVERFLOW, RR_ETIMEOUT, RR_EBUSY, RR_EINTERNAL = range(9)
+STATUS_NAMES = ["RR_OK", "RR_EINVAL", "RR_ENOMEM", "RR_ECUDA", "RR_EFORMAT", "RR_EOVERFLOW", "RR_ETIMEOUT",
+                "RR_EBUSY", "RR_EINTERNAL"]
+RR_BEAM, RR_BEAM_ES, RR_DOUBLING, RR_DOUBLING_ES, RR_GREEDY, RR_GREEDY_ES = range(6)
+VARIANTS = {"beam": RR_BEAM, "beam_es": RR_BEAM_ES, "doubling": RR_DOUBLING, "doubling_es": RR_DOUBLING_ES,
+            "greedy": RR_GREEDY, "greedy_es": RR_GREEDY_ES}
+RR_U8, RR_I8, RR_F32 = 0, 1, 2
+RR_L2, RR_IP = 0, 1
+RR_PREC_EXACT, RR_PREC_BF16, RR_PREC_FP8 = 0, 1, 2
+RR_FLAG_TRUNCATED, RR_FLAG_EARLY_STOPPED, RR_FLAG_PHASE2 = 1, 2, 4
+
+# every symbol include/rr.h declares (checked by the ABI test)
+EXPORTS = ["rr_params_init", "rr_create_index", "rr_load_index", "rr_free_index", "rr_index_info_get",
+           "rr_range_search", "rr_brute_force", "rr_result_free", "rr_last_error", "rr_last_profile"]
+
+
+class RRError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else status, msg))
+        self.status = status
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("beam", ctypes.c_int32), ("b_max", ctypes.c_int32), ("es_visit_limit", ctypes.c_int32),
+                ("es_radius_mode", ctypes.c_int32), ("es_radius", ctypes.c_double), ("precision", ctypes.c_int32),
+                ("recheck_eps", ctypes.c_float), ("persistent", ctypes.c_int32), ("collect_stats", ctypes.c_int32),
+                ("max_results_total", ctypes.c_int64), ("tile_hint", ctypes.c_int32),
+                ("profile", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6)]
+
+
+class Profile(ctypes.Structure):
+    _fields_ = [("beam_ms", ctypes.c_float), ("phase2_ms", ctypes.c_float), ("output_ms", ctypes.c_float),
+                ("total_ms", ctypes.c_float), ("launches", ctypes.c_int32), ("phase2_steps", ctypes.c_int32),
+                ("phase2_queries", ctypes.c_int32), ("valid", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class QueryStats(ctypes.Structure):
+    _fields_ = [("visits_beam", ctypes.c_int32), ("visits_phase2", ctypes.c_int32), ("distinct", ctypes.c_int32),
+                ("rounds", ctypes.c_int32), ("final_beam", ctypes.c_int32), ("evals", ctypes.c_int32)]
+
+
+STATS_DTYPE = np.dtype([(n, np.int32) for n, _ in QueryStats._fields_])
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("nq", ctypes.c_int64), ("total", ctypes.c_int64), ("offsets", ctypes.c_void_p),
+                ("ids", ctypes.c_void_p), ("dists", ctypes.c_void_p), ("dist_dtype", ctypes.c_int32),
+                ("on_device", ctypes.c_int32), ("flags", ctypes.c_void_p), ("stats", ctypes.c_void_p),
+                ("_stream", ctypes.c_void_p), ("_device", ctypes.c_int32), ("_pad", ctypes.c_int32)]
+
+
+class IndexInfo(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("d", ctypes.c_int32), ("dtype", ctypes.c_int32), ("metric", ctypes.c_int32),
+                ("R", ctypes.c_int32), ("start", ctypes.c_int64), ("device_bytes", ctypes.c_int64),
+                ("row_stride", ctypes.c_int32), ("device", ctypes.c_int32)]
+
+
+_lib = None
+
+
+def load_library(path: str | None = None):
+    """Load librr.so.  There is no fallback: a missing or unloadable library raises."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB
+    if not os.path.exists(path):
+        raise RuntimeError("librr.so is not built (%s); run paper_2502_13245_gb300.build()" % path)
+    L = ctypes.CDLL(path)
+    P, I32, I64, D = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+    L.rr_params_init.restype = None
+    L.rr_params_init.argtypes = [P]
+    L.rr_create_index.restype = ctypes.c_int
+    L.rr_create_index.argtypes = [P, I64, I32, I32, I32, P, I32, I64, I32, I32, P]
+    L.rr_load_index.restype = ctypes.c_int
+    L.rr_load_index.argtypes = [ctypes.c_char_p, I32, P]
+    L.rr_free_index.restype = ctypes.c_int
+    L.rr_free_index.argtypes = [P]
+    L.rr_index_info_get.restype = ctypes.c_int
+    L.rr_index_info_get.argtypes = [P, P]
+    L.rr_range_search.restype = ctypes.c_int
+    L.rr_range_search.argtypes = [P, P, I64, P, D, I32, P, P, I32, P]
+    L.rr_brute_force.restype = ctypes.c_int
+    L.rr_brute_force.argtypes = [P, P, I64, P, D, P, I32, P]
+    L.rr_result_free.restype = ctypes.c_int
+    L.rr_result_free.argtypes = [P]
+    L.rr_last_error.restype = ctypes.c_char_p
+    L.rr_last_error.argtypes = []
+    L.rr_last_profile.restype = ctypes.c_int
+    L.rr_last_profile.argtypes = [P, P]
+    _lib = L
+    return L
+
+
+def _check(status):
+    if status != RR_OK:
+        raise RRError(status, rr_last_error())
+
+
+# ------------------------------------------------------------------------------------------------
+# one-to-one entry points
+# ------------------------------------------------------------------------------------------------
+
+def rr_last_error() -> str:
+    return load_library().rr_last_error().decode("utf8", "replace")
+
+
+def rr_params_init(**overrides) -> Params:
+    p = Params()
+    load_library().rr_params_init(ctypes.byref(p))
+    for k, v in overrides.items():
+        if not hasattr(p, k):
+            raise TypeError("unknown parameter %s" % k)
+        setattr(p, k, v)
+    return p
+
+
+def _ptr_and_device(a):
+    """(pointer, is_device, keepalive) for a numpy array or torch tensor."""
+    if isinstance(a, np.ndarray):
+        a = np.ascontiguousarray(a)
+        return a.ctypes.data, False, a
+    import torch
+    if isinstance(a, torch.Tensor):
+        a = a.contiguous()
+        return a.data_ptr(), a.is_cuda, a
+    raise TypeError("expected numpy array or torch tensor")
+
+
+_DT = {np.dtype(np.uint8): RR_U8, np.dtype(np.int8): RR_I8, np.dtype(np.float32): RR_F32}
+
+
+def _dtype_code(a):
+    if isinstance(a, np.ndarray):
+        return _DT[a.dtype]
+    import torch
+    return {torch.uint8: RR_U8, torch.int8: RR_I8, torch.float32: RR_F32}[a.dtype]
+
+
+def rr_create_index(vectors, adjacency, start, metric=RR_L2, device=0, validate=True):
+    """vectors: n x d (uint8/int8/float32), adjacency: n x R uint32 (0xFFFFFFFF pads), host or device."""
+    vp, _, vk = _ptr_and_device(vectors)
+    if isinstance(adjacency, np.ndarray):
+        adjacency = np.ascontiguousarray(adjacency, dtype=np.uint32)
+    ap, _, ak = _ptr_and_device(adjacency)
+    n, d = vk.shape
+    R = ak.shape[1]
+    h = ctypes.c_void_p()
+    _check(load_library().rr_create_index(vp, n, d, _dtype_code(vk), metric, ap, R, int(start), device,
+                                          1 if validate else 0, ctypes.byref(h)))
+    return h
+
+
+def rr_load_index(path: str, device=0):
+    h = ctypes.c_void_p()
+    _check(load_library().rr_load_index(path.encode(), device, ctypes.byref(h)))
+    return h
+
+
+def rr_free_index(handle):
+    _check(load_library().rr_free_index(handle))
+
+
+def rr_index_info_get(handle) -> IndexInfo:
+    info = IndexInfo()
+    _check(load_library().rr_index_info_get(handle, ctypes.byref(info)))
+    return info
+
+
+def _radii(nq, radius):
+    if np.ndim(radius) == 0:
+        return None, float(radius), None
+    r = np.ascontiguousarray(np.asarray(radius, dtype=np.float64).reshape(-1))
+    assert r.shape[0] == nq
+    return r.ctypes.data, 0.0, r
+
+
+def _stream_of(qdev, stream):
+    if stream is not None:
+        return stream
+    if qdev:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return None
+
+
+def rr_range_search(handle, queries, radius, variant=RR_GREEDY_ES, params: Params | None = None, stream=None,
+                    result_on_device=False, check=True) -> tuple[int, Result]:
+    """Returns (status, Result).  `radius`: scalar or one per query."""
+    qp, qdev, qk = _ptr_and_device(queries)
+    nq = qk.shape[0]
+    rp, rs, rk = _radii(nq, radius)
+    res = Result()
+    v = VARIANTS[variant] if isinstance(variant, str) else int(variant)
+    st = load_library().rr_range_search(handle, qp, nq, rp, rs, v, ctypes.byref(params) if params else None,
+                                        _stream_of(qdev, stream), 1 if result_on_device else 0, ctypes.byref(res))
+    if check and st not in (RR_OK, RR_EOVERFLOW):
+        raise RRError(st, rr_last_error())
+    return st, res
+
+
+def rr_brute_force(handle, queries, radius, stream=None, result_on_device=False) -> Result:
+    qp, qdev, qk = _ptr_and_device(queries)
+    nq = qk.shape[0]
+    rp, rs, rk = _radii(nq, radius)
+    res = Result()
+    _check(load_library().rr_brute_force(handle, qp, nq, rp, rs, _stream_of(qdev, stream),
+                                         1 if result_on_device else 0, ctypes.byref(res)))
+    return res
+
+
+def rr_last_profile(handle) -> Profile:
+    p = Profile()
+    _check(load_library().rr_last_profile(handle, ctypes.byref(p)))
+    return p
+
+
+def rr_result_free(res: Result):
+    _check(load_library().rr_result_free(ctypes.byref(res)))
+
+
+# ------------------------------------------------------------------------------------------------
+# convenience
+# ------------------------------------------------------------------------------------------------
+
+class RangeResult:
+    """Host copy of a result: offsets (nq+1), ids, dists, flags, optional stats."""
+
+    def __init__(self, res: Result, status=RR_OK):
+        self.status = status
+        nq, tot = res.nq, res.total
+        if res.on_device:
+            raise ValueError("RangeResult wraps host results")
+
+        def arr(p, ct, n, dt):
+            if n == 0 or not p:
+                return np.zeros(0, dt)
+            return np.ctypeslib.as_array(ctypes.cast(p, ctypes.POINTER(ct)), (n,)).copy()
+
+        self.offsets = arr(res.offsets, ctypes.c_int64, nq + 1, np.int64)
+        if nq + 1 > len(self.offsets):
+            self.offsets = np.zeros(nq + 1, np.int64)
+        self.ids = arr(res.ids, ctypes.c_uint32, tot, np.uint32)
+        self.dists = arr(res.dists, ctypes.c_float if res.dist_dtype else ctypes.c_int32, tot,
+                         np.float32 if res.dist_dtype else np.int32)
+        self.flags = arr(res.flags, ctypes.c_uint8, nq, np.uint8)
+        self.stats = None
+        if res.stats:
+            raw = np.ctypeslib.as_array(ctypes.cast(res.stats, ctypes.POINTER(ctypes.c_int32)), (nq * 6,)).copy()
+            self.stats = raw.view(STATS_DTYPE)
+        rr_result_free(res)
+
+    def __len__(self):
+        return len(self.offsets) - 1
+
+    def query(self, i):
+        s, e = self.offsets[i], self.offsets[i + 1]
+        return self.ids[s:e], self.dists[s:e]
+
+    def lists(self):
+        return [self.ids[self.offsets[i]:self.offsets[i + 1]] for i in range(len(self))]
+
+
+class Index:
+    """Owns an rr_index handle."""
+
+    def __init__(self, handle):
+        self.h = handle
+        self.info = rr_index_info_get(handle)
+
+    @classmethod
+    def from_arrays(cls, X, adj, start, metric=RR_L2, device=0, validate=True):
+        return cls(rr_create_index(X, adj, start, metric, device, validate))
+
+    @classmethod
+    def load(cls, path, device=0):
+        return cls(rr_load_index(path, device))
+
+    def close(self):
+        if self.h:
+            rr_free_index(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def range_search(self, Q, radius, variant="greedy_es", stream=None, **params) -> RangeResult:
+        p = rr_params_init(**params)
+        st, res = rr_range_search(self.h, Q, radius, variant, p, stream=stream, result_on_device=False)
+        return RangeResult(res, st)
+
+    def brute_force(self, Q, radius, stream=None) -> RangeResult:
+        return RangeResult(rr_brute_force(self.h, Q, radius, stream=stream))

@@ -1,0 +1,185 @@
+// k_greedy.cu -- Alg. 2 GreedySearch for the queries whose beam phase filled
+// the beam with in-range points (Alg. 6: |N| = b).
+//
+// Alg. 2 returns S plus every point reachable from S through out-edges whose
+// endpoints lie within r; the argmin order only fixes the visit order, not the
+// set.  So it runs here as a level-synchronous BFS over all greedy queries at
+// once: an item is one (query slot, point) pair to visit; a level kernel
+// expands every item of the current level with one warp each and appends the
+// newly found in-range points to a global item list.  Each query slot owns an
+// exact bitmap of n bits ("seen": ids already in F or already evaluated), so
+// every point is evaluated at most once per query and enters F at most once.
+// The items of a slot are exactly its result set V.
+#include "rr_common.cuh"
+
+namespace rr {
+
+namespace {
+
+template <bool COUNT>
+__global__ void greedy_init_kernel(GreedyArgs g) {
+    const int b = g.s.beam;
+    const int64_t total = (int64_t)g.ng * b;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        int32_t slot = (int32_t)(t / b);
+        int32_t i = (int32_t)(t % b);
+        int32_t qi = g.qlist[slot];
+        uint64_t k = g.s.res_keys[(size_t)qi * b + i];
+        g.item_key[t] = k;
+        g.item_slot[t] = slot;
+        mark_bit(g.seen + (size_t)slot * g.seen_words, key_id(k));
+        if (i == 0) {
+            g.slot_count[slot] = b;
+            g.slot_trunc[slot] = 0;
+        }
+    }
+}
+
+template <int DT, int CPL, bool COUNT>
+__global__ void __launch_bounds__(256) greedy_level_kernel(GreedyArgs g) {
+    extern __shared__ __align__(16) uint8_t smem_raw[];
+    constexpr int UN = CPL == 1 ? 8 : (CPL == 2 ? 4 : 2);
+    const SearchArgs &a = g.s;
+    const int lane = lane_id();
+    const int warp = threadIdx.x >> 5;
+    const int wpc = blockDim.x >> 5;
+    const int R = a.R;
+    uint64_t *ckey = reinterpret_cast<uint64_t *>(smem_raw) + (size_t)warp * R;
+    uint32_t *cid = reinterpret_cast<uint32_t *>(reinterpret_cast<uint64_t *>(smem_raw) + (size_t)wpc * R) +
+                    (size_t)warp * R;
+    const int64_t nw = (int64_t)gridDim.x * wpc;
+    for (int64_t it = g.begin + (int64_t)blockIdx.x * wpc + warp; it < g.end; it += nw) {
+        const int32_t slot = g.item_slot[it];
+        const uint32_t p = key_id(g.item_key[it]);
+        const int32_t qi = g.qlist[slot];
+        uint4 q[CPL];
+        load_query<CPL>(a, a.queries + (size_t)qi * a.row_stride, q);
+        const uint32_t rk = a.rkey[qi];
+        uint32_t *seen = g.seen + (size_t)slot * g.seen_words;
+        // f in N_out(p*) \ V, each evaluated once per query (exact bitmap)
+        const uint32_t *row = a.adj + (size_t)p * R;
+        int nc = 0;
+        for (int e0 = 0; e0 < R; e0 += 32) {
+            int e = e0 + lane;
+            uint32_t j = e < R ? __ldg(row + e) : kSent;
+            bool v = j < (uint32_t)a.n && mark_bit(seen, j);
+            unsigned m = __ballot_sync(0xffffffffu, v);
+            if (v) cid[nc + __popc(m & lanemask_lt())] = j;
+            nc += __popc(m);
+        }
+        __syncwarp();
+        if (nc > 0) {
+            eval_candidates<DT, CPL, UN>(a, q, cid, nc, ckey);
+            __syncwarp();
+            int dd = 0;
+            if (COUNT) {
+                uint32_t *cb = a.count_bits + (size_t)qi * a.words_per_q;
+                for (int c = lane; c < nc; c += 32) dd += mark_bit(cb, cid[c]);
+            }
+            // if d(f, q) <= r: F <- F u {f}
+            int added = 0;
+            for (int c0 = 0; c0 < nc; c0 += 32) {
+                int c = c0 + lane;
+                uint64_t k = c < nc ? ckey[c] : kEmpty;
+                bool in = c < nc && key_dk(k) <= rk;
+                unsigned m = __ballot_sync(0xffffffffu, in);
+                int cnt = __popc(m);
+                if (cnt == 0) continue;
+                unsigned long long basepos = 0;
+                if (lane == 0) basepos = atomicAdd(g.tail, (unsigned long long)cnt);
+                basepos = __shfl_sync(0xffffffffu, basepos, 0);
+                if (in) {
+                    unsigned long long pos = basepos + __popc(m & lanemask_lt());
+                    if (pos < (unsigned long long)g.cap) {
+                        g.item_key[pos] = k;
+                        g.item_slot[pos] = slot;
+                    } else {
+                        g.slot_trunc[slot] = 1;
+                    }
+                }
+                long long room = (long long)g.cap - (long long)basepos;
+                added += room <= 0 ? 0 : (room < cnt ? (int)room : cnt);
+            }
+            if (COUNT) {
+                for (int o = 16; o > 0; o >>= 1) dd += __shfl_xor_sync(0xffffffffu, dd, o);
+            }
+            if (lane == 0) {
+                if (added) atomicAdd(g.slot_count + slot, added);
+                if (a.stats) {
+                    atomicAdd(&a.stats[qi].evals, nc);
+                    if (COUNT) atomicAdd(&a.stats[qi].distinct, dd);
+                }
+            }
+        }
+        if (lane == 0 && a.stats) atomicAdd(&a.stats[qi].visits_phase2, 1);
+        __syncwarp();
+    }
+}
+
+template <int DT, int CPL>
+rr_status level_t(const GreedyArgs &g, cudaStream_t st) {
+    const int wpc = 8;
+    size_t smem = (size_t)wpc * g.s.R * 12;
+    int64_t items = g.end - g.begin;
+    int64_t blocks = (items + wpc - 1) / wpc;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    if (blocks < 1) blocks = 1;
+    if (g.s.count_bits) {
+        auto k = greedy_level_kernel<DT, CPL, true>;
+        k<<<(unsigned)blocks, 32 * wpc, smem, st>>>(g);
+    } else {
+        auto k = greedy_level_kernel<DT, CPL, false>;
+        k<<<(unsigned)blocks, 32 * wpc, smem, st>>>(g);
+    }
+    RR_CUDA(cudaGetLastError());
+    note_launch();
+    return RR_OK;
+}
+
+__global__ void set_counts_kernel(int32_t *res_count, uint8_t *flags, const int32_t *qlist, const int32_t *slot_count,
+                                  const int32_t *slot_trunc, int32_t n) {
+    for (int32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
+        int32_t q = qlist[s];
+        res_count[q] = slot_count[s];
+        if (slot_trunc && slot_trunc[s]) flags[q] |= RR_FLAG_TRUNCATED;
+    }
+}
+
+}  // namespace
+
+rr_status launch_greedy_init(const GreedyArgs &g, cudaStream_t st, int) {
+    int64_t total = (int64_t)g.ng * g.s.beam;
+    if (total == 0) return RR_OK;
+    int64_t blocks = (total + 255) / 256;
+    if (blocks > 4096) blocks = 4096;
+    greedy_init_kernel<false><<<(unsigned)blocks, 256, 0, st>>>(g);
+    RR_CUDA(cudaGetLastError());
+    note_launch();
+    return RR_OK;
+}
+
+rr_status launch_greedy_level(const GreedyArgs &g, cudaStream_t st, int dtype_code) {
+    if (g.end <= g.begin) return RR_OK;
+    const int cpl = (g.s.row_chunks + 31) / 32;
+    switch (dtype_code) {
+        case DT_U8: return level_t<DT_U8, 1>(g, st);
+        case DT_I8: return level_t<DT_I8, 1>(g, st);
+        case DT_F32:
+            if (cpl <= 1) return level_t<DT_F32, 1>(g, st);
+            if (cpl <= 2) return level_t<DT_F32, 2>(g, st);
+            return level_t<DT_F32, 4>(g, st);
+    }
+    set_error("greedy phase: unsupported element type %d", dtype_code);
+    return RR_EINVAL;
+}
+
+rr_status launch_set_counts(int32_t *res_count, uint8_t *flags, const int32_t *qlist, const int32_t *slot_count,
+                            const int32_t *slot_trunc, int32_t n, cudaStream_t st) {
+    if (n <= 0) return RR_OK;
+    set_counts_kernel<<<(n + 255) / 256, 256, 0, st>>>(res_count, flags, qlist, slot_count, slot_trunc, n);
+    RR_CUDA(cudaGetLastError());
+    note_launch();
+    return RR_OK;
+}
+
+}  // namespace rr

@@ -1,0 +1,186 @@
+// k_output.cu -- assembly of the per-query results into one CSR (the output
+// of Alg. 6 / Alg. 3 for the whole batch): count -> exclusive scan -> copy or
+// scatter -> per-query sort by (distance, id) -> decode keys into ids and
+// distances.
+#include "rr_common.cuh"
+
+namespace rr {
+
+namespace {
+
+// Exclusive scan of int32 counts into int64 offsets[0..n], one CTA, chunked.
+__global__ void __launch_bounds__(1024) scan_kernel(const int32_t *counts, int64_t n, int64_t *offsets) {
+    __shared__ int64_t wsum[32];
+    __shared__ int64_t carry;
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    if (t == 0) carry = 0;
+    __syncthreads();
+    for (int64_t base = 0; base < n; base += 1024) {
+        int64_t i = base + t;
+        int64_t v = i < n ? (int64_t)counts[i] : 0;
+        int64_t x = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            int64_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) wsum[w] = x;
+        __syncthreads();
+        if (w == 0) {
+            int64_t s = wsum[lane];
+            for (int o = 1; o < 32; o <<= 1) {
+                int64_t y = __shfl_up_sync(0xffffffffu, s, o);
+                if (lane >= o) s += y;
+            }
+            wsum[lane] = s;  // inclusive prefix of warp sums
+        }
+        __syncthreads();
+        int64_t incl = x + (w > 0 ? wsum[w - 1] : 0) + carry;
+        if (i < n) offsets[i] = incl - v;
+        __syncthreads();
+        if (t == 1023) carry = incl;
+        __syncthreads();
+    }
+    if (t == 0) offsets[n] = carry;
+}
+
+__device__ __forceinline__ void decode_to(const OutArgs &o, int64_t pos, uint64_t k) {
+    if (pos < 0 || pos >= o.total) {  // never write outside the result arrays
+        atomicExch(o.error, 4);
+        return;
+    }
+    o.ids[pos] = key_id(k);
+    uint32_t dk = key_dk(k);
+    if (o.dist_is_float) reinterpret_cast<float *>(o.dists)[pos] = dval_f32(dk);
+    else reinterpret_cast<int32_t *>(o.dists)[pos] = dval_i32(dk);
+}
+
+// Warp per listed slot: copy `count[slot]` sorted keys from keys[slot*stride]
+// to the CSR range of query qlist[slot] (qlist == nullptr: slot = query, and
+// queries flagged RR_FLAG_PHASE2 are skipped -- their results come later).
+__global__ void copy_slots_kernel(OutArgs o, const uint64_t *keys, int64_t stride, const int32_t *count,
+                                  const int32_t *qlist, int32_t nlist) {
+    const int lane = lane_id();
+    const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t s = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); s < nlist; s += nw) {
+        int64_t q = qlist ? qlist[s] : s;
+        if (!qlist && (o.flags[q] & RR_FLAG_PHASE2)) continue;
+        int32_t c = count[s];
+        int64_t off = o.offsets[q];
+        const uint64_t *src = keys + (size_t)s * stride;
+        for (int i = lane; i < c; i += 32) decode_to(o, off + i, src[i]);
+    }
+}
+
+__global__ void scatter_items_kernel(OutArgs o, const uint64_t *item_key, const int32_t *item_slot, int64_t nitems,
+                                     const int32_t *qlist, int32_t *cursor, uint64_t *tmp) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nitems; t += (int64_t)gridDim.x * blockDim.x) {
+        int32_t s = item_slot[t];
+        int64_t q = qlist[s];
+        int64_t pos = o.offsets[q] + atomicAdd(cursor + s, 1);
+        if (pos < 0 || pos >= o.offsets[q + 1]) {
+            atomicExch(o.error, 4);
+            continue;
+        }
+        tmp[pos] = item_key[t];
+    }
+}
+
+// Bitonic sort with "flip" first stages, so every compare puts the smaller key
+// at the lower index and a virtual +inf padding past m never moves.
+__device__ void bitonic_sort_smem(uint64_t *a, int m) {
+    int P = 1;
+    while (P < m) P <<= 1;
+    for (int k = 2; k <= P; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = threadIdx.x; i < P / 2; i += blockDim.x) {
+                // i-th compare pair of this stage
+                int lo, hi;
+                if (j == (k >> 1)) {  // flip stage: pair (x, x ^ (k-1)) inside each k-block
+                    int blk = i / (k >> 1), off = i % (k >> 1);
+                    lo = blk * k + off;
+                    hi = blk * k + (k - 1 - off);
+                } else {
+                    int blk = i / j, off = i % j;
+                    lo = blk * 2 * j + off;
+                    hi = lo + j;
+                }
+                if (hi < m) {
+                    uint64_t x = a[lo], y = a[hi];
+                    if (y < x) { a[lo] = y; a[hi] = x; }
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// CTA per listed query: sort its CSR segment of tmp keys and decode it.
+// Segments up to smem_cap keys are sorted in shared memory, longer ones in
+// place in global memory with the same network.
+__global__ void __launch_bounds__(1024) sort_segments_kernel(OutArgs o, uint64_t *tmp, const int32_t *qlist,
+                                                             int32_t nlist, int smem_cap) {
+    extern __shared__ __align__(16) uint8_t smem_raw[];
+    uint64_t *sk = reinterpret_cast<uint64_t *>(smem_raw);
+    for (int32_t s = blockIdx.x; s < nlist; s += gridDim.x) {
+        int64_t q = qlist[s];
+        int64_t off = o.offsets[q];
+        int m = (int)(o.offsets[q + 1] - off);
+        if (m <= 0) continue;
+        uint64_t *seg = tmp + off;
+        uint64_t *a = seg;
+        if (m <= smem_cap) {
+            for (int i = threadIdx.x; i < m; i += blockDim.x) sk[i] = seg[i];
+            __syncthreads();
+            a = sk;
+        }
+        bitonic_sort_smem(a, m);
+        for (int i = threadIdx.x; i < m; i += blockDim.x) decode_to(o, off + i, a[i]);
+        __syncthreads();
+    }
+}
+
+}  // namespace
+
+rr_status launch_scan(const int32_t *counts, int64_t n, int64_t *offsets, cudaStream_t st) {
+    scan_kernel<<<1, 1024, 0, st>>>(counts, n, offsets);
+    RR_CUDA(cudaGetLastError());
+    note_launch();
+    return RR_OK;
+}
+
+rr_status launch_copy_slots(const OutArgs &o, const uint64_t *keys, int64_t stride, const int32_t *count,
+                            const int32_t *qlist, int32_t nlist, cudaStream_t st) {
+    if (nlist <= 0) return RR_OK;
+    int64_t blocks = (nlist + 7) / 8;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    copy_slots_kernel<<<(unsigned)blocks, 256, 0, st>>>(o, keys, stride, count, qlist, nlist);
+    RR_CUDA(cudaGetLastError());
+    note_launch();
+    return RR_OK;
+}
+
+rr_status launch_scatter_items(const OutArgs &o, const uint64_t *item_key, const int32_t *item_slot, int64_t nitems,
+                               const int32_t *qlist, int32_t *cursor, uint64_t *tmp, cudaStream_t st) {
+    if (nitems <= 0) return RR_OK;
+    int64_t blocks = (nitems + 255) / 256;
+    if (blocks > 152 * 32) blocks = 152 * 32;
+    scatter_items_kernel<<<(unsigned)blocks, 256, 0, st>>>(o, item_key, item_slot, nitems, qlist, cursor, tmp);
+    RR_CUDA(cudaGetLastError());
+    note_launch();
+    return RR_OK;
+}
+
+rr_status launch_sort_segments(const OutArgs &o, uint64_t *tmp, const int32_t *qlist, int32_t nlist, int64_t,
+                               cudaStream_t st) {
+    if (nlist <= 0) return RR_OK;
+    const int smem_cap = 16384;  // keys: 128 KB of shared memory
+    size_t smem = (size_t)smem_cap * 8;
+    RR_CUDA(cudaFuncSetAttribute(sort_segments_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int blocks = nlist < 152 * 2 ? nlist : 152 * 2;
+    sort_segments_kernel<<<blocks, 1024, smem, st>>>(o, tmp, qlist, nlist, smem_cap);
+    RR_CUDA(cudaGetLastError());
+    note_launch();
+    return RR_OK;
+}
+
+}  // namespace rr

@@ -264,7 +264,7 @@ CONFIGS = {
     # 10,000 x 128 uint8, 100 centres, 1,000 queries, R=32 L=64 alpha=1.2
     "c0": Config("c0", 10_000, 128, 1_000, "u8", M_L2, 100, 12.0, 500, 32, 64, 1.2, 2, 0, 2.0),
     # 1,000,000 x 128 uint8, 1,000 centres, 10,000 queries, R=64 L=128 alpha=1.2
-    "c1": Config("c1", 1_000_000, 128, 10_000, "u8", M_L2, 1000, 12.0, 5000, 64, 128, 1.2, 1, 1, 2.0),
+    "c1": Config("c1", 1_000_000, 128, 10_000, "u8", M_L2, 1000, 12.0, 5000, 64, 128, 1.2, 2, 1, 2.0),
     # 1,000,000 x 200 fp32 unit vectors, inner product, 10,000 queries, R=64 L=128 alpha=1.0
     "c2": Config("c2", 1_000_000, 200, 10_000, "f32", M_IP, 1000, 0.06, 5000, 64, 128, 1.0, 1, 2, 0.01),
 }
