@@ -305,6 +305,7 @@ def main():
     with ClockSampler(dev) as clk:
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.nvtx.range_push("timed")
         e0.record(stream)
         for _ in range(args.steps):
             st, res = rr.rr_range_search(gi.h, Qd, ds.radius, variant, pp, stream=sh, result_on_device=True)
@@ -314,6 +315,7 @@ def main():
             rr.rr_result_free(res)
         e1.record(stream)
         torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
     step_ms = e0.elapsed_time(e1) / args.steps
     if ws > 1:
         from paper_2502_13245_gb300 import multi
@@ -360,7 +362,7 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
             "config": {"workload": "%s: n=%d d=%d uint8 L2, nq=%d per GPU, Vamana R=%d L=%d alpha=%.2f" % (
                 cfg.name, cfg.n, cfg.d, cfg.nq, cfg.R, cfg.L_build, cfg.alpha),
-                "variant": variant, "beam": beam, "ap": best["ap"],
+                "variant": variant, "beam": beam, "ap": best["ap"], "es_vl": form[1], "es_radius_over_r": form[2],
                 "plain_beam_form": None if plain_best is None else {
                     "beam": plain_best["beam"], "qps": plain_best["qps"], "ap": plain_best["ap"]},
                 "l2_policy": "index (vectors + adjacency %.0f MB) larger than L2" % (
