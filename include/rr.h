@@ -203,6 +203,31 @@ typedef struct {
 
 rr_status rr_last_profile(rr_index *index, rr_profile *out);
 
+/* Beam search without any memory allocation (the paper has no counterpart:
+ * this is a deployment variant of RR_BEAM / RR_BEAM_ES, Alg. 1 + Alg. 5 plus
+ * the range filter).  For callers that may not allocate -- e.g. code running
+ * under a memory budget reserved up front, inside a host callback, or after
+ * start-up under a no-allocation policy.  rr_range_search allocates its
+ * result and grows per-index scratch; this call allocates nothing.
+ *   queries     nq x d device array of the index's element type
+ *   radius      one radius for every query (metric units)
+ *   variant     RR_BEAM or RR_BEAM_ES; params may be NULL (defaults; b <= 512)
+ *   out_counts  nq int32 (device): |N| of each query
+ *   out_ids     nq x b uint32 (device): N of query i in out_ids[i*b ..], sorted
+ *               by (distance, id); slots past out_counts[i] hold 0xFFFFFFFF
+ *   out_dists   nq x b int32 (8-bit indexes) or float32 (fp32 indexes), device
+ * Intermediate data live in one static device array of 32 MiB per GPU that
+ * loads the library, held until the process exits; a batch that needs more
+ * (about nq*(b*8 + 16) bytes, plus nq*row for unaligned queries) is rejected
+ * with RR_EINVAL -- split it.  The first call on a device looks the array's
+ * address up (cudaGetSymbolAddress); make it before any stream capture.
+ * Calls share the array: calls whose work overlaps on the GPU race, so
+ * serialise them.  Returns after the stream has finished the call's work.
+ * Results equal rr_range_search's for the same variant and beam. */
+rr_status rr_beam_search_noalloc(rr_index *index, const void *queries, int64_t nq, double radius, int32_t variant,
+                                 const rr_params *params, void *stream, int32_t *out_counts, uint32_t *out_ids,
+                                 void *out_dists);
+
 /* Free the arrays of a result (host or device) and zero the struct. */
 rr_status rr_result_free(rr_result *result);
 

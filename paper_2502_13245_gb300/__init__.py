@@ -31,7 +31,8 @@ RR_FLAG_TRUNCATED, RR_FLAG_EARLY_STOPPED, RR_FLAG_PHASE2 = 1, 2, 4
 
 # every symbol include/rr.h declares (checked by the ABI test)
 EXPORTS = ["rr_params_init", "rr_create_index", "rr_load_index", "rr_free_index", "rr_index_info_get",
-           "rr_range_search", "rr_brute_force", "rr_result_free", "rr_last_error", "rr_last_profile"]
+           "rr_range_search", "rr_brute_force", "rr_result_free", "rr_last_error", "rr_last_profile",
+           "rr_beam_search_noalloc"]
 
 
 class RRError(RuntimeError):
@@ -111,6 +112,8 @@ def load_library(path: str | None = None):
     L.rr_last_error.argtypes = []
     L.rr_last_profile.restype = ctypes.c_int
     L.rr_last_profile.argtypes = [P, P]
+    L.rr_beam_search_noalloc.restype = ctypes.c_int
+    L.rr_beam_search_noalloc.argtypes = [P, P, I64, D, I32, P, P, P, P, P]
     _lib = L
     return L
 
@@ -230,6 +233,24 @@ def rr_brute_force(handle, queries, radius, stream=None, result_on_device=False)
     _check(load_library().rr_brute_force(handle, qp, nq, rp, rs, _stream_of(qdev, stream),
                                          1 if result_on_device else 0, ctypes.byref(res)))
     return res
+
+
+def rr_beam_search_noalloc(handle, queries, radius, variant, params, out_counts, out_ids, out_dists, stream=None):
+    """Allocation-free beam search into caller-owned device arrays (torch CUDA tensors).
+
+    For callers that may not allocate device memory while they run: the outputs
+    must already exist (out_counts: nq int32, out_ids: nq x b int32/uint32,
+    out_dists: nq x b int32 or float32) and the library uses only a fixed static
+    scratch array.  Returns the status (raises on errors other than RR_OK)."""
+    qp, qdev, qk = _ptr_and_device(queries)
+    nq = qk.shape[0]
+    v = VARIANTS[variant] if isinstance(variant, str) else int(variant)
+    st = load_library().rr_beam_search_noalloc(handle, qp, nq, float(radius), v,
+                                               ctypes.byref(params) if params else None,
+                                               _stream_of(qdev, stream), out_counts.data_ptr(), out_ids.data_ptr(),
+                                               out_dists.data_ptr())
+    _check(st)
+    return st
 
 
 def rr_last_profile(handle) -> Profile:
