@@ -173,7 +173,7 @@ def run_reference(args, cfg, ds):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="own", choices=["own", "reference"])
     ap.add_argument("--config", default="c1")
@@ -184,6 +184,8 @@ def main():
     ap.add_argument("--ref-beam", type=int, default=16)
     ap.add_argument("--ref-sample", type=int, default=300)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--fixed", default="", help="VARIANT:BEAM[:VL:ESR] -- skip the sweep and time this form")
+    ap.add_argument("--no-tune", action="store_true", help="keep the library's default launch shape")
     args = ap.parse_args()
 
     ws, rank, local = dist_env()
@@ -251,6 +253,10 @@ def main():
             forms += [(variant, vl, esr) for vl, esr in ES_GRID]
         else:
             forms.append((variant, 20, 1.0))
+    if args.fixed:
+        f = args.fixed.split(":")
+        forms = [(f[0], int(f[2]) if len(f) > 2 else 20, float(f[3]) if len(f) > 3 else 1.0)]
+        args.beams = f[1]
     for form in forms:
         reached = 0
         last_ap = -1.0
@@ -292,8 +298,16 @@ def main():
         int(st_full["distinct"].sum()) * row + nq * row
 
     # timed region: K steps, inputs resident in HBM, results left on the device
-    p = params(form, beam)
-    pp = params(form, beam, profile=1)
+    # launch shape of the beam kernel for this form (results do not depend on it)
+    tuned = {}
+    if not args.no_tune:
+        from paper_2502_13245_gb300 import autotune
+        tuned, _ = autotune.tune(gi, Qd, ds.radius, variant, beam, stream=stream, reps=2,
+                                 base_params={"es_visit_limit": form[1], "es_radius_mode": 1,
+                                              "es_radius": float(ds.radius) * form[2]},
+                                 log=log if rank == 0 else None)
+    p = params(form, beam, **tuned)
+    pp = params(form, beam, profile=1, **tuned)
     for _ in range(max(3, args.warmup)):
         st, res = rr.rr_range_search(gi.h, Qd, ds.radius, variant, p, stream=sh, result_on_device=True)
         rr.rr_result_free(res)
@@ -363,6 +377,8 @@ def main():
             "config": {"workload": "%s: n=%d d=%d uint8 L2, nq=%d per GPU, Vamana R=%d L=%d alpha=%.2f" % (
                 cfg.name, cfg.n, cfg.d, cfg.nq, cfg.R, cfg.L_build, cfg.alpha),
                 "variant": variant, "beam": beam, "ap": best["ap"], "es_vl": form[1], "es_radius_over_r": form[2],
+                "launch_shape": tuned or "library default",
+                "beam_phase_evals_per_distinct": float(st_beam["evals"].sum()) / max(1, int(st_beam["distinct"].sum())),
                 "plain_beam_form": None if plain_best is None else {
                     "beam": plain_best["beam"], "qps": plain_best["qps"], "ap": plain_best["ap"]},
                 "l2_policy": "index (vectors + adjacency %.0f MB) larger than L2" % (

@@ -92,7 +92,8 @@ typedef struct {
     int64_t max_results_total; /* cap on the summed result count (0 = default 1<<28) */
     int32_t tile_hint;         /* warps per CTA for the beam kernel (0 = library choice) */
     int32_t profile;           /* 1: record per-phase device times, see rr_last_profile */
-    int32_t reserved[6];
+    int32_t seen_log2;         /* log2 slots of the beam kernel's seen table, 5..14 (0 = library choice) */
+    int32_t reserved[5];
 } rr_params;
 
 /* Exact per-query counters (collect_stats = 1).  visits_* count |V| of the

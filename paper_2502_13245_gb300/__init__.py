@@ -46,7 +46,7 @@ class Params(ctypes.Structure):
                 ("es_radius_mode", ctypes.c_int32), ("es_radius", ctypes.c_double), ("precision", ctypes.c_int32),
                 ("recheck_eps", ctypes.c_float), ("persistent", ctypes.c_int32), ("collect_stats", ctypes.c_int32),
                 ("max_results_total", ctypes.c_int64), ("tile_hint", ctypes.c_int32),
-                ("profile", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6)]
+                ("profile", ctypes.c_int32), ("seen_log2", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
 
 
 class Profile(ctypes.Structure):

@@ -3,28 +3,33 @@
 // the phase-2 classification of Alg. 6 / Alg. 3 (|N| = b -> greedy or
 // doubling).  One warp per query.
 //
-// Per-warp shared memory: the beam B (sorted keys, double buffered), the
-// candidate list of the current expansion, and a lossy direct-mapped "seen"
-// table.  The table only filters ids that were inserted into B before; that is
-// exact because (a) B never holds an id twice (merges drop equal keys) and (b)
-// an id trimmed out of B has b smaller keys in B from then on, so re-inserting
-// it is a no-op after the next trim.  A table miss therefore only costs a
-// repeated distance evaluation, never a different B.  |V| is counted exactly.
+// Per-warp shared memory: the beam B (keys sorted by (distance, id), the low
+// bit marks V), the candidates of the current expansion, and a lossy
+// direct-mapped "seen" table.  The table only filters ids whose distance was
+// evaluated before; that is exact because (a) B never holds an id twice
+// (merges drop equal keys) and (b) an id that left B, or was refused by a full
+// B, has b smaller keys in B from then on (B's b-th key only decreases), so
+// offering it again changes nothing.  A table miss only costs a repeated
+// distance evaluation, never a different B.  |V| is counted exactly.
+//
+// The merge of the (few) new keys into B is done in place: with the new keys
+// sorted, old entry i moves right by the number of new keys below it, so only
+// the suffix after the first insertion point is touched, chunk by chunk from
+// the end.  The index of the first unvisited entry (p* of Alg. 1) is carried
+// across iterations instead of rescanning B.
+#include <algorithm>
+
 #include "rr_common.cuh"
 
 namespace rr {
 
 namespace {
 
-struct WarpSmem {
-    uint64_t *bcur, *bnxt, *ckey, *skey;
-    uint32_t *cid, *hash;
-};
-
 __host__ __device__ inline size_t warp_smem_bytes(int bmax, int R, int hlg) {
-    return (size_t)2 * bmax * 8 + (size_t)2 * R * 8 + (size_t)R * 4 + ((size_t)4 << hlg);
+    return (size_t)bmax * 8 + (size_t)2 * R * 8 + (size_t)3 * R * 4 + ((size_t)4 << hlg);
 }
 
+// number of a[t] with (a[t] | 1) < k1
 __device__ __forceinline__ int lower_bound_or1(const uint64_t *a, int n, uint64_t k1) {
     int lo = 0, hi = n;
     while (lo < hi) {
@@ -35,71 +40,70 @@ __device__ __forceinline__ int lower_bound_or1(const uint64_t *a, int n, uint64_
     return lo;
 }
 
-// B <- top-b(B u C): C = ckey[0..nc) (unsorted, visited bit clear).  Candidates
-// that cannot enter (B full and not smaller than B[b-1]) or whose key is
-// already in B are dropped first.  Writes the merged beam to Bn and returns
-// its size, or -1 when nothing changed (Bn untouched).
-__device__ int merge_into_beam(const uint64_t *B, uint64_t *Bn, int nb, int b, uint64_t *ckey, uint64_t *skey,
-                               int nc) {
+// number of v[t] <= x (v non-decreasing)
+__device__ __forceinline__ int upper_bound_i32(const int32_t *v, int n, int x) {
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if (v[mid] <= x) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// first index >= from with the visited bit clear, or n
+__device__ __forceinline__ int next_unvisited(const uint64_t *B, int n, int from) {
     const int lane = lane_id();
-    const uint64_t last = (nb == b) ? (B[b - 1] | 1ull) : kEmpty;
-    int ns = 0;
-    for (int base = 0; base < nc; base += 32) {
-        int c = base + lane;
-        uint64_t k = c < nc ? ckey[c] : kEmpty;
-        bool keep = c < nc && (k | 1ull) < last;
-        if (keep) {
-            int lb = lower_bound_or1(B, nb, k | 1ull);
-            if (lb < nb && (B[lb] | 1ull) == (k | 1ull)) keep = false;
-        }
-        unsigned m = __ballot_sync(0xffffffffu, keep);
-        if (keep) skey[ns + __popc(m & lanemask_lt())] = k;
-        ns += __popc(m);
+    for (int b0 = from; b0 < n; b0 += 32) {
+        int i = b0 + lane;
+        unsigned m = __ballot_sync(0xffffffffu, i < n && !(B[i] & 1ull));
+        if (m) return b0 + __ffs(m) - 1;
     }
-    __syncwarp();
-    if (ns == 0) return -1;
-    // sort the survivors by rank (keys are distinct)
-    for (int c = lane; c < ns; c += 32) {
-        uint64_t k = skey[c];
-        int r = 0;
-        for (int t = 0; t < ns; t++) r += skey[t] < k;
-        ckey[r] = k;
-    }
-    __syncwarp();
-    for (int c = lane; c < ns; c += 32) {
-        uint64_t k = ckey[c];
-        int pos = c + lower_bound_or1(B, nb, k | 1ull);
-        if (pos < b) Bn[pos] = k;
-    }
-    for (int i = lane; i < nb; i += 32) {
-        uint64_t k = B[i];
-        int pos = i + lower_bound_or1(ckey, ns, k | 1ull);
-        if (pos < b) Bn[pos] = k;
-    }
-    __syncwarp();
-    return min(b, nb + ns);
+    return n;
 }
 
 template <int DT, int CPL, int BMAX, bool COUNT>
-__global__ void __launch_bounds__(256) beam_kernel(SearchArgs a, int hlg) {
+__device__ __forceinline__ void search_query(const SearchArgs &a, int hlg, int64_t qi, uint8_t *base);
+
+// One warp per query.  persistent = 0: warp w of CTA c takes query c*warps + w.
+// persistent = 1: a grid sized to the resident capacity; every warp takes the
+// next query from a device counter until the batch is done, so warps freed by
+// cheap (e.g. early-stopped) queries move on to the rest of the batch.
+template <int DT, int CPL, int BMAX, bool COUNT>
+__global__ void __launch_bounds__(256, 3) beam_kernel(SearchArgs a, int hlg, int persistent, int32_t *next_q) {
     extern __shared__ __align__(16) uint8_t smem_raw[];
-    constexpr int UN = CPL == 1 ? 8 : (CPL == 2 ? 4 : 2);
     const int lane = lane_id();
     const int warp = threadIdx.x >> 5;
-    const int64_t qi = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
-    if (qi >= a.nq) return;  // whole warp leaves; the kernel has no block barriers
+    uint8_t *base = smem_raw + (size_t)warp * warp_smem_bytes(BMAX, a.R, hlg);
+    int64_t qi = 0;
+    if (!persistent) qi = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
+    else if (lane == 0) qi = atomicAdd(next_q, 1);
+    qi = __shfl_sync(0xffffffffu, qi, 0);
+    // whole warps leave together; the kernel has no block barriers
+    while (qi < a.nq) {
+        search_query<DT, CPL, BMAX, COUNT>(a, hlg, qi, base);
+        if (!persistent) break;
+        __syncwarp();
+        if (lane == 0) qi = atomicAdd(next_q, 1);
+        qi = __shfl_sync(0xffffffffu, qi, 0);
+    }
+}
+
+template <int DT, int CPL, int BMAX, bool COUNT>
+__device__ __forceinline__ void search_query(const SearchArgs &a, int hlg, int64_t qi, uint8_t *base) {
+    constexpr int UN = CPL == 1 ? 8 : (CPL == 2 ? 4 : 2);
+    const int lane = lane_id();
     const int R = a.R;
     const int b = a.beam;
     const int H = 1 << hlg;
 
-    uint8_t *base = smem_raw + (size_t)warp * warp_smem_bytes(BMAX, R, hlg);
-    WarpSmem s;
-    s.bcur = reinterpret_cast<uint64_t *>(base);
-    s.bnxt = s.bcur + BMAX;
-    s.ckey = s.bnxt + BMAX;
-    s.skey = s.ckey + R;
-    s.cid = reinterpret_cast<uint32_t *>(s.skey + R);
-    s.hash = s.cid + R;
+    uint64_t *B = reinterpret_cast<uint64_t *>(base);
+    uint64_t *ckey = B + BMAX;       // candidate keys, then the sorted survivors
+    uint64_t *skey = ckey + R;       // survivors before sorting
+    uint32_t *cid = reinterpret_cast<uint32_t *>(skey + R);
+    int32_t *lbs = reinterpret_cast<int32_t *>(cid + R);  // insertion point of each sorted survivor
+    int32_t *slb = lbs + R;                                // insertion point of each unsorted survivor
+    uint32_t *hash = reinterpret_cast<uint32_t *>(slb + R);
 
     uint4 q[CPL];
     load_query<CPL>(a, a.queries + (size_t)qi * a.row_stride, q);
@@ -107,95 +111,155 @@ __global__ void __launch_bounds__(256) beam_kernel(SearchArgs a, int hlg) {
     const uint32_t ek = a.eskey[qi];
     uint32_t *cbits = COUNT ? a.count_bits + (size_t)qi * a.words_per_q : nullptr;
 
-    for (int i = lane; i < H; i += 32) s.hash[i] = kSent;
+    for (int i = lane; i < H; i += 32) hash[i] = kSent;
     // B <- S = {start}
     const uint32_t dk0 = eval_one<DT, CPL>(a, q, a.start);
     int distinct = 0;
+    __syncwarp();
     if (lane == 0) {
-        s.bcur[0] = make_key(dk0, a.start);
+        B[0] = make_key(dk0, a.start);
+        hash[hslot(a.start, hlg)] = a.start;
         if (COUNT) distinct += mark_bit(cbits, a.start);
     }
     __syncwarp();
-    if (lane == 0) s.hash[hslot(a.start, hlg)] = a.start;
-    int nb = 1, nvis = 0, evals = 1;
+    int nb = 1, cur = 0, nvis = 0, evals = 1;
     bool stopped = false;
     int64_t guard = 0;
-    __syncwarp();
+    // adjacency row of the likely next p* (the next unvisited entry), loaded while the
+    // current candidates are evaluated; used only if that entry is indeed chosen
+    uint32_t pre[4];
+    uint32_t pre_id = kSent;
 
-    for (;;) {
-        // p* <- argmin over B \ V: B is sorted, so the first unvisited entry
-        int pidx = -1;
-        for (int b0 = 0; b0 < nb; b0 += 32) {
-            int i = b0 + lane;
-            bool un = i < nb && !(s.bcur[i] & 1ull);
-            unsigned m = __ballot_sync(0xffffffffu, un);
-            if (m) { pidx = b0 + __ffs(m) - 1; break; }
-        }
-        if (pidx < 0) break;
-        const uint64_t pk = s.bcur[pidx];
+    while (cur < nb) {
+        // p* <- argmin over B \ V = B[cur] (B sorted, everything before cur visited)
+        const uint64_t pk = B[cur];
         // Alg. 5: closest of B outside r, |V| >= vl, d(p*) outside esr
-        if (a.use_es && key_dk(s.bcur[0]) > rk && nvis >= a.es_vl && key_dk(pk) > ek) { stopped = true; break; }
-        if (++guard > a.n + 1) {  // every point is visited at most once
-            if (lane == 0) atomicExch(a.error, 1);
+        if (a.use_es && key_dk(B[0]) > rk && nvis >= a.es_vl && key_dk(pk) > ek) { stopped = true; break; }
+        const uint32_t p = key_id(pk);
+        if (++guard > a.n + 1 || p >= (uint32_t)a.n) {  // cannot happen for a validated index
+            if (lane == 0) atomicExch(a.error, p >= (uint32_t)a.n ? 3 : 1);
             break;
         }
         __syncwarp();
-        if (lane == 0) s.bcur[pidx] = pk | 1ull;  // V <- V u {p*}
+        if (lane == 0) B[cur] = pk | 1ull;  // V <- V u {p*}
         nvis++;
-        const uint32_t p = key_id(pk);
-        if (p >= (uint32_t)a.n) {  // cannot happen for a validated index; never index out of bounds
-            if (lane == 0) atomicExch(a.error, 3);
-            break;
-        }
+        __syncwarp();
+        const int nxt = next_unvisited(B, nb, cur + 1);
         // N_out(p*) minus ids seen before (see the file comment)
-        const uint32_t *row = a.adj + (size_t)p * R;
+        uint32_t row4[4];
+        if (p == pre_id) {
+#pragma unroll
+            for (int k = 0; k < 4; k++) row4[k] = pre[k];
+        } else {
+            const uint32_t *row = a.adj + (size_t)p * R;
+#pragma unroll
+            for (int k = 0; k < 4; k++) row4[k] = (32 * k + lane < R) ? __ldg(row + 32 * k + lane) : kSent;
+        }
+        pre_id = kSent;
+        if (nxt < nb) {
+            const uint32_t pn = key_id(B[nxt]);
+            if (pn < (uint32_t)a.n) {
+                const uint32_t *row = a.adj + (size_t)pn * R;
+#pragma unroll
+                for (int k = 0; k < 4; k++) pre[k] = (32 * k + lane < R) ? __ldg(row + 32 * k + lane) : kSent;
+                pre_id = pn;
+            }
+        }
         int nc = 0;
-        for (int e0 = 0; e0 < R; e0 += 32) {
-            int e = e0 + lane;
-            uint32_t j = e < R ? __ldg(row + e) : kSent;
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            if (32 * k >= R) break;  // warp-uniform
+            uint32_t j = row4[k];
             bool v = j < (uint32_t)a.n;  // also drops the 0xFFFFFFFF padding
             uint32_t sl = 0;
             if (v) {
                 sl = hslot(j, hlg);
-                v = s.hash[sl] != j;
+                v = hash[sl] != j;
             }
             unsigned m = __ballot_sync(0xffffffffu, v);
             if (v) {
-                s.hash[sl] = j;
-                s.cid[nc + __popc(m & lanemask_lt())] = j;
+                hash[sl] = j;
+                cid[nc + __popc(m & lanemask_lt())] = j;
             }
             nc += __popc(m);
             __syncwarp();
         }
-        if (nc == 0) continue;
+        if (nc == 0) { cur = nxt; continue; }
         evals += nc;
-        eval_candidates<DT, CPL, UN>(a, q, s.cid, nc, s.ckey);
+        eval_candidates<DT, CPL, UN>(a, q, cid, nc, ckey);
         __syncwarp();
         if (COUNT) {
             int dd = 0;
-            for (int c = lane; c < nc; c += 32) dd += mark_bit(cbits, s.cid[c]);
+            for (int c = lane; c < nc; c += 32) dd += mark_bit(cbits, cid[c]);
             distinct += dd;
         }
-        // B <- top-b(B u new)
-        int nn = merge_into_beam(s.bcur, s.bnxt, nb, b, s.ckey, s.skey, nc);
-        if (nn >= 0) {
-            nb = nn;
-            uint64_t *t = s.bcur;
-            s.bcur = s.bnxt;
-            s.bnxt = t;
+        // keys that can enter: below B[b-1] when B is full, and not already in B
+        const uint64_t last = (nb == b) ? (B[b - 1] | 1ull) : kEmpty;
+        int ns = 0;
+        for (int c0 = 0; c0 < nc; c0 += 32) {
+            int c = c0 + lane;
+            uint64_t k = c < nc ? ckey[c] : kEmpty;
+            bool keep = c < nc && (k | 1ull) < last;
+            int lb = 0;
+            if (keep) {
+                lb = lower_bound_or1(B, nb, k | 1ull);
+                keep = !(lb < nb && (B[lb] | 1ull) == (k | 1ull));
+            }
+            unsigned m = __ballot_sync(0xffffffffu, keep);
+            if (keep) {
+                const int o = ns + __popc(m & lanemask_lt());
+                skey[o] = k;
+                slb[o] = lb;
+            }
+            ns += __popc(m);
         }
         __syncwarp();
+        if (ns == 0) { cur = nxt; continue; }
+        // sort the survivors (distinct keys) by rank; each keeps its insertion point in B
+        for (int c = lane; c < ns; c += 32) {
+            uint64_t k = skey[c];
+            int r = 0;
+            for (int t = 0; t < ns; t++) r += skey[t] < k;
+            ckey[r] = k;
+            lbs[r] = slb[c];
+        }
+        __syncwarp();
+        const int lb0 = lbs[0];
+        // B <- top-b(B u survivors): shift the suffix [lb0, nb) right, last chunk first
+        for (int hi = nb; hi > lb0;) {
+            const int lo = max(lb0, hi - 32);
+            const int i = lo + lane;
+            uint64_t k = 0;
+            int dst = b;
+            if (i < hi) {
+                k = B[i];
+                dst = i + upper_bound_i32(lbs, ns, i);
+            }
+            __syncwarp();
+            if (dst < b) B[dst] = k;
+            __syncwarp();
+            hi = lo;
+        }
+        for (int c = lane; c < ns; c += 32) {
+            int pos = lbs[c] + c;
+            if (pos < b) B[pos] = ckey[c];
+        }
+        __syncwarp();
+        // first unvisited entry: the smallest survivor, or the old next one after its shift
+        const int posn = nxt < nb ? nxt + upper_bound_i32(lbs, ns, nxt) : 0x7fffffff;
+        nb = min(b, nb + ns);
+        cur = min(min(posn, lb0), nb);
     }
 
     // N = {n in B : d(n, q) <= r}: a prefix of the sorted beam
     int cnt = 0;
     for (int b0 = 0; b0 < nb; b0 += 32) {
         int i = b0 + lane;
-        bool in = i < nb && key_dk(s.bcur[i]) <= rk;
+        bool in = i < nb && key_dk(B[i]) <= rk;
         cnt += __popc(__ballot_sync(0xffffffffu, in));
     }
     uint64_t *out = a.res_keys + (size_t)qi * b;
-    for (int i = lane; i < cnt; i += 32) out[i] = s.bcur[i] & ~1ull;
+    for (int i = lane; i < cnt; i += 32) out[i] = B[i] & ~1ull;
     if (COUNT) {
         for (int o = 16; o > 0; o >>= 1) distinct += __shfl_xor_sync(0xffffffffu, distinct, o);
     }
@@ -221,22 +285,33 @@ __global__ void __launch_bounds__(256) beam_kernel(SearchArgs a, int hlg) {
     }
 }
 
-template <int DT, int CPL, int BMAX>
-rr_status launch_t(const SearchArgs &a, int wpc, int hlg, cudaStream_t st) {
-    size_t smem = (size_t)wpc * warp_smem_bytes(BMAX, a.R, hlg);
-    dim3 grid((unsigned)((a.nq + wpc - 1) / wpc)), block(32 * wpc);
-    if (a.count_bits) {
-        auto k = beam_kernel<DT, CPL, BMAX, true>;
-        RR_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k<<<grid, block, smem, st>>>(a, hlg);
-    } else {
-        auto k = beam_kernel<DT, CPL, BMAX, false>;
-        RR_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k<<<grid, block, smem, st>>>(a, hlg);
+template <int DT, int CPL, int BMAX, bool COUNT>
+rr_status launch_k(const SearchArgs &a, int wpc, int hlg, cudaStream_t st) {
+    auto k = beam_kernel<DT, CPL, BMAX, COUNT>;
+    const size_t smem = (size_t)wpc * warp_smem_bytes(BMAX, a.R, hlg);
+    RR_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int64_t blocks = (a.nq + wpc - 1) / wpc;
+    if (a.persistent) {
+        int dev = 0, sms = 0, per_sm = 0;
+        RR_CUDA(cudaGetDevice(&dev));
+        RR_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        RR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 32 * wpc, smem));
+        blocks = std::min<int64_t>(blocks, (int64_t)std::max(1, per_sm) * sms);
     }
+    k<<<(unsigned)blocks, 32 * wpc, smem, st>>>(a, hlg, a.persistent, a.next_q);
     RR_CUDA(cudaGetLastError());
     note_launch();
     return RR_OK;
+}
+
+template <int DT, int CPL, int BMAX>
+rr_status launch_t(const SearchArgs &a, int wpc, int hlg, cudaStream_t st) {
+    if (a.persistent && !a.next_q) {
+        set_error("beam phase: persistent launch without a work counter");
+        return RR_EINTERNAL;
+    }
+    if (a.count_bits) return launch_k<DT, CPL, BMAX, true>(a, wpc, hlg, st);
+    return launch_k<DT, CPL, BMAX, false>(a, wpc, hlg, st);
 }
 
 template <int DT, int CPL>
@@ -252,11 +327,15 @@ rr_status launch_b(const SearchArgs &a, int wpc, int hlg, cudaStream_t st) {
 
 }  // namespace
 
-int beam_hash_lg(int beam) { return beam <= 64 ? 10 : (beam <= 256 ? 11 : 12); }
+int beam_hash_lg(int beam) { return beam <= 256 ? 10 : 11; }
 
 rr_status launch_beam(const SearchArgs &a, int wpc, cudaStream_t st, int dtype_code) {
     if (a.nq == 0) return RR_OK;
-    const int hlg = beam_hash_lg(a.beam);
+    const int hlg = a.hash_lg > 0 ? a.hash_lg : beam_hash_lg(a.beam);
+    if (hlg < 5 || hlg > 14) {
+        set_error("beam phase: seen-table size 2^%d out of [2^5, 2^14]", hlg);
+        return RR_EINVAL;
+    }
     const int cpl = (a.row_chunks + 31) / 32;
     switch (dtype_code) {
         case DT_U8: return launch_b<DT_U8, 1>(a, wpc, hlg, st);

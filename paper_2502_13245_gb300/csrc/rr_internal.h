@@ -108,6 +108,9 @@ struct SearchArgs {
     uint32_t *count_bits;     // exact distinct-id bitmaps (stats mode), nq x words_per_q, or nullptr
     int64_t words_per_q;
     int32_t *error;           // device status word (0 = fine)
+    int32_t hash_lg;          // log2 of the beam kernel's seen-table slots (0 = library default)
+    int32_t persistent;       // 1: resident grid, queries taken from *next_q (must start at 0)
+    int32_t *next_q;
 };
 
 rr_status launch_beam(const SearchArgs &a, int warps_per_cta, cudaStream_t s, int dtype_code);

@@ -485,6 +485,9 @@ extern "C" rr_status rr_range_search(rr_index *ix, const void *queries, int64_t 
     SearchArgs &a = S.a;
     a.use_es = use_es ? 1 : 0;
     a.es_vl = P.es_visit_limit;
+    a.hash_lg = P.seen_log2;
+    a.persistent = P.persistent ? 1 : 0;
+    a.next_q = a.p2_count + 2;  // zeroed with the other counters in stage()
     a.phase2 = greedy ? 1 : (doubling ? 2 : 0);
     const bool prof = P.profile != 0;
     const int64_t l0 = launches_so_far();

@@ -94,6 +94,16 @@ def test_c0_exact_counters(rr, c0, c0_index, c0_oracle, variant):
     assert_same(res, o_ids, o_d, len(c0.Q))
 
 
+@pytest.mark.parametrize("shape", [dict(persistent=1), dict(tile_hint=2, seen_log2=6), dict(tile_hint=8, seen_log2=12),
+                                   dict(persistent=1, tile_hint=1, seen_log2=5)])
+def test_launch_shapes_do_not_change_results(rr, c0, c0_index, c0_oracle, shape):
+    """Warps per CTA, seen-table size and the persistent work queue are performance knobs only."""
+    for variant, beam in (("greedy_es", 32), ("beam", 64), ("doubling", 16)):
+        o_ids, o_d, _ = oracle_run(c0_oracle, c0, variant, beam)
+        res = c0_index.range_search(c0.Q, c0.radius, variant, beam=beam, **shape)
+        assert_same(res, o_ids, o_d, len(c0.Q))
+
+
 def test_ragged_and_tiny_batches(rr, c0, c0_index, c0_oracle):
     for nq in (1, 2, 37, 129):
         Q = c0.Q[:nq]
