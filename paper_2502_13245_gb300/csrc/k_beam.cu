@@ -4,8 +4,9 @@
 // doubling).  One warp per query.
 //
 // Per-warp shared memory: the beam B (keys sorted by (distance, id), the low
-// bit marks V), the candidates of the current expansion, and a lossy
-// direct-mapped "seen" table.  The table only filters ids whose distance was
+// bit marks V), the candidates of the current expansion, and a lossy two-way
+// set-associative "seen" table (a set keeps its two most recent ids; a slot
+// only ever holds an id that was evaluated).  The table only filters ids whose distance was
 // evaluated before; that is exact because (a) B never holds an id twice
 // (merges drop equal keys) and (b) an id that left B, or was refused by a full
 // B, has b smaller keys in B from then on (B's b-th key only decreases), so
@@ -105,20 +106,32 @@ __device__ __forceinline__ void search_query(const SearchArgs &a, int hlg, int64
     int32_t *slb = lbs + R;                                // insertion point of each unsorted survivor
     uint32_t *hash = reinterpret_cast<uint32_t *>(slb + R);
 
+    constexpr bool LP = is_lowp(DT);
     uint4 q[CPL];
-    load_query<CPL>(a, a.queries + (size_t)qi * a.row_stride, q);
+    float qf[16];
+    float qn2 = 0.f;
+    if constexpr (LP) {
+        load_query_lp<DT>(a, reinterpret_cast<const float *>(a.queries + (size_t)qi * a.row_stride), qf);
+        qn2 = query_norm2_lp(a, qf);
+    } else {
+        load_query<CPL>(a, a.queries + (size_t)qi * a.row_stride, q);
+    }
     const uint32_t rk = a.rkey[qi];
     const uint32_t ek = a.eskey[qi];
+    // low precision: approximate distances above r + slack are certainly out of range
+    const uint32_t rks = LP ? slack_key(a, rk, qn2) : rk;
     uint32_t *cbits = COUNT ? a.count_bits + (size_t)qi * a.words_per_q : nullptr;
 
     for (int i = lane; i < H; i += 32) hash[i] = kSent;
     // B <- S = {start}
-    const uint32_t dk0 = eval_one<DT, CPL>(a, q, a.start);
+    uint32_t dk0;
+    if constexpr (LP) dk0 = eval_one_lp<DT>(a, qf, qn2, a.start);
+    else dk0 = eval_one<DT, CPL>(a, q, a.start);
     int distinct = 0;
     __syncwarp();
     if (lane == 0) {
         B[0] = make_key(dk0, a.start);
-        hash[hslot(a.start, hlg)] = a.start;
+        hash[hslot(a.start, hlg - 1) << 1] = a.start;
         if (COUNT) distinct += mark_bit(cbits, a.start);
     }
     __syncwarp();
@@ -134,7 +147,7 @@ __device__ __forceinline__ void search_query(const SearchArgs &a, int hlg, int64
         // p* <- argmin over B \ V = B[cur] (B sorted, everything before cur visited)
         const uint64_t pk = B[cur];
         // Alg. 5: closest of B outside r, |V| >= vl, d(p*) outside esr
-        if (a.use_es && key_dk(B[0]) > rk && nvis >= a.es_vl && key_dk(pk) > ek) { stopped = true; break; }
+        if (a.use_es && key_dk(B[0]) > rks && nvis >= a.es_vl && key_dk(pk) > ek) { stopped = true; break; }
         const uint32_t p = key_id(pk);
         if (++guard > a.n + 1 || p >= (uint32_t)a.n) {  // cannot happen for a validated index
             if (lane == 0) atomicExch(a.error, p >= (uint32_t)a.n ? 3 : 1);
@@ -171,13 +184,17 @@ __device__ __forceinline__ void search_query(const SearchArgs &a, int hlg, int64
             if (32 * k >= R) break;  // warp-uniform
             uint32_t j = row4[k];
             bool v = j < (uint32_t)a.n;  // also drops the 0xFFFFFFFF padding
-            uint32_t sl = 0;
+            uint32_t sl = 0, old = kSent;
             if (v) {
-                sl = hslot(j, hlg);
-                v = hash[sl] != j;
+                // two-way set: slot 2s holds the most recent id of the set, 2s+1 the one before
+                sl = hslot(j, hlg - 1) << 1;
+                old = hash[sl];
+                v = old != j && hash[sl + 1] != j;
             }
             unsigned m = __ballot_sync(0xffffffffu, v);
+            __syncwarp();
             if (v) {
+                hash[sl + 1] = old;
                 hash[sl] = j;
                 cid[nc + __popc(m & lanemask_lt())] = j;
             }
@@ -186,7 +203,8 @@ __device__ __forceinline__ void search_query(const SearchArgs &a, int hlg, int64
         }
         if (nc == 0) { cur = nxt; continue; }
         evals += nc;
-        eval_candidates<DT, CPL, UN>(a, q, cid, nc, ckey);
+        if constexpr (LP) eval_candidates_lp<DT, 8>(a, qf, qn2, cid, nc, ckey);
+        else eval_candidates<DT, CPL, UN>(a, q, cid, nc, ckey);
         __syncwarp();
         if (COUNT) {
             int dd = 0;
@@ -251,12 +269,17 @@ __device__ __forceinline__ void search_query(const SearchArgs &a, int hlg, int64
         cur = min(min(posn, lb0), nb);
     }
 
-    // N = {n in B : d(n, q) <= r}: a prefix of the sorted beam
+    // N = {n in B : d(n, q) <= r}: a prefix of the sorted beam.  Low precision: the
+    // prefix within r + slack is re-checked in exact fp32 and re-sorted by exact keys.
     int cnt = 0;
     for (int b0 = 0; b0 < nb; b0 += 32) {
         int i = b0 + lane;
-        bool in = i < nb && key_dk(B[i]) <= rk;
+        bool in = i < nb && key_dk(B[i]) <= rks;
         cnt += __popc(__ballot_sync(0xffffffffu, in));
+    }
+    if constexpr (LP) {
+        evals += cnt;
+        cnt = exact_filter_sort<CPL, UN>(a, qi, B, cnt, rk, cid, ckey, R);
     }
     uint64_t *out = a.res_keys + (size_t)qi * b;
     for (int i = lane; i < cnt; i += 32) out[i] = B[i] & ~1ull;
@@ -341,6 +364,9 @@ rr_status launch_beam(const SearchArgs &a, int wpc, cudaStream_t st, int dtype_c
         case DT_U8: return launch_b<DT_U8, 1>(a, wpc, hlg, st);
         case DT_I8: return launch_b<DT_I8, 1>(a, wpc, hlg, st);
         case DT_F32:
+            // low-precision traversal: CPL = 4 covers the exact rows of every d <= 512
+            if (a.prec == RR_PREC_BF16) return launch_b<DT_BF16, 4>(a, wpc, hlg, st);
+            if (a.prec == RR_PREC_FP8) return launch_b<DT_FP8, 4>(a, wpc, hlg, st);
             if (cpl <= 1) return launch_b<DT_F32, 1>(a, wpc, hlg, st);
             if (cpl <= 2) return launch_b<DT_F32, 2>(a, wpc, hlg, st);
             return launch_b<DT_F32, 4>(a, wpc, hlg, st);

@@ -92,9 +92,18 @@ __global__ void __launch_bounds__(128) round_kernel(DoublingRound d) {
 
     const int32_t slot = d.act[i];
     const int32_t qi = d.qlist[slot];
+    constexpr bool LP = is_lowp(DT);
     uint4 q[CPL];
-    load_query<CPL>(a, a.queries + (size_t)qi * a.row_stride, q);
+    float qf[16];
+    float qn2 = 0.f;
+    if constexpr (LP) {
+        load_query_lp<DT>(a, reinterpret_cast<const float *>(a.queries + (size_t)qi * a.row_stride), qf);
+        qn2 = query_norm2_lp(a, qf);
+    } else {
+        load_query<CPL>(a, a.queries + (size_t)qi * a.row_stride, q);
+    }
     const uint32_t rk = a.rkey[qi], ek = a.eskey[qi];
+    const uint32_t rks = LP ? slack_key(a, rk, qn2) : rk;  // approximate keys above rks are out of range
     uint64_t *M = d.bA + (size_t)i * b;
     uint64_t *M2 = d.bB + (size_t)i * b;
     uint64_t *V = d.v + (size_t)i * d.v_cap;
@@ -105,7 +114,9 @@ __global__ void __launch_bounds__(128) round_kernel(DoublingRound d) {
     // B <- top-b(S)
     int nM;
     if (d.first) {
-        uint32_t dk0 = eval_one<DT, CPL>(a, q, a.start);
+        uint32_t dk0;
+        if constexpr (LP) dk0 = eval_one_lp<DT>(a, qf, qn2, a.start);
+        else dk0 = eval_one<DT, CPL>(a, q, a.start);
         if (lane == 0) {
             M[0] = make_key(dk0, a.start);
             mark_bit(seen, a.start);
@@ -152,7 +163,7 @@ __global__ void __launch_bounds__(128) round_kernel(DoublingRound d) {
         if (a.use_es) {
             uint64_t mn = M[0] | 1ull;
             if (nI > 0 && (s.I[0] | 1ull) < mn) mn = s.I[0] | 1ull;
-            if (key_dk(mn) > rk && nvis >= a.es_vl && key_dk(pk) > ek) { stopped = true; break; }
+            if (key_dk(mn) > rks && nvis >= a.es_vl && key_dk(pk) > ek) { stopped = true; break; }
         }
         if (++guard > a.n + 1) {
             if (lane == 0) atomicExch(a.error, 2);
@@ -180,7 +191,8 @@ __global__ void __launch_bounds__(128) round_kernel(DoublingRound d) {
         __syncwarp();
         if (nc == 0) continue;
         evals += nc;
-        eval_candidates<DT, CPL, UN>(a, q, s.cid, nc, s.ckey);
+        if constexpr (LP) eval_candidates_lp<DT, 8>(a, qf, qn2, s.cid, nc, s.ckey);
+        else eval_candidates<DT, CPL, UN>(a, q, s.cid, nc, s.ckey);
         __syncwarp();
         if (cbits) {
             int dd = 0;
@@ -273,12 +285,16 @@ __global__ void __launch_bounds__(128) round_kernel(DoublingRound d) {
         M = M2;
         M2 = t;
     }
-    // N = {n in B : d <= r}
+    // N = {n in B : d <= r} (low precision: exact fp32 recheck of the prefix within r + slack)
     int cnt = 0;
     for (int b0 = 0; b0 < nM; b0 += 32) {
         int t = b0 + lane;
-        bool in = t < nM && key_dk(M[t]) <= rk;
+        bool in = t < nM && key_dk(M[t]) <= rks;
         cnt += __popc(__ballot_sync(0xffffffffu, in));
+    }
+    if constexpr (LP) {
+        evals += cnt;
+        cnt = exact_filter_sort<CPL, UN>(a, qi, M, cnt, rk, s.cid, s.ckey, R);
     }
     const bool cont = !stopped && !overflow && cnt == b && !d.last;
     if (!cont) {
@@ -414,6 +430,8 @@ rr_status launch_doubling_round(const DoublingRound &d, cudaStream_t st, int dty
         case DT_U8: return round_t<DT_U8, 1>(d, st);
         case DT_I8: return round_t<DT_I8, 1>(d, st);
         case DT_F32:
+            if (d.s.prec == RR_PREC_BF16) return round_t<DT_BF16, 4>(d, st);
+            if (d.s.prec == RR_PREC_FP8) return round_t<DT_FP8, 4>(d, st);
             if (cpl <= 1) return round_t<DT_F32, 1>(d, st);
             if (cpl <= 2) return round_t<DT_F32, 2>(d, st);
             return round_t<DT_F32, 4>(d, st);

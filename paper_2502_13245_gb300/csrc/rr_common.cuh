@@ -9,6 +9,8 @@
 // low "visited" bit marks V membership of beam entries; compares that must
 // ignore it use (key | 1).  Ids are < 2^31.
 #pragma once
+#include <cuda_fp16.h>
+#include <cuda_fp8.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -194,6 +196,206 @@ __device__ __forceinline__ unsigned lanemask_lt() { return (1u << lane_id()) - 1
 __device__ __forceinline__ int mark_bit(uint32_t *bits, uint32_t id) {
     uint32_t m = 1u << (id & 31);
     return (atomicOr(bits + (id >> 5), m) & m) ? 0 : 1;
+}
+
+// -------------------------------------------------------------------------------------------
+// Low-precision traversal (fp32 indexes).  A traversal row is split in 16-byte
+// chunks over lp_lpv lanes: a chunk holds 8 BF16 or 16 FP8 values.  The lane
+// keeps the fp32 query values of its chunk in qf[16] (one chunk per lane, so
+// d <= 256 for BF16 and d <= 512 for FP8).  Products are accumulated in fp32.
+// -------------------------------------------------------------------------------------------
+__host__ __device__ constexpr bool is_lowp(int DT) { return DT == DT_BF16 || DT == DT_FP8; }
+
+template <int DT>
+__device__ __forceinline__ void load_query_lp(const SearchArgs &a, const float *qrow, float (&qf)[16]) {
+    constexpr int E = DT == DT_BF16 ? 8 : 16;
+    const int sub = lane_id() & (a.lp_lpv - 1);
+#pragma unroll
+    for (int j = 0; j < 16; j++) qf[j] = 0.f;
+#pragma unroll
+    for (int k = 0; k < 1; k++) {  // one chunk per lane: lp_chunks <= 32
+        const int ch = sub + k * a.lp_lpv;
+#pragma unroll
+        for (int j = 0; j < E; j++) {
+            const int e = ch * E + j;
+            qf[k * E + j] = (ch < a.lp_chunks && e < a.d) ? qrow[e] : 0.f;
+        }
+    }
+}
+
+// ||q||^2 from the lane-distributed query values (every lane group holds the whole query)
+__device__ __forceinline__ float query_norm2_lp(const SearchArgs &a, const float (&qf)[16]) {
+    float s = 0.f;
+#pragma unroll
+    for (int j = 0; j < 16; j++) s = fmaf(qf[j], qf[j], s);
+    return group_sum(s, a.lp_lpv);
+}
+
+__device__ __forceinline__ float bf16_lo(uint32_t w) { return __uint_as_float(w << 16); }
+__device__ __forceinline__ float bf16_hi(uint32_t w) { return __uint_as_float(w & 0xffff0000u); }
+
+// one 16-byte chunk against 16 query values starting at qf[o]: BF16 -> L2 or dot, FP8 -> dot
+template <int DT>
+__device__ __forceinline__ void lp_chunk(const uint4 &v, const float *q, bool l2, float &acc) {
+    const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+    if (DT == DT_BF16) {
+#pragma unroll
+        for (int t = 0; t < 4; t++) {
+            const float x0 = bf16_lo(w[t]), x1 = bf16_hi(w[t]);
+            if (l2) {
+                const float d0 = q[2 * t] - x0, d1 = q[2 * t + 1] - x1;
+                acc = fmaf(d0, d0, acc);
+                acc = fmaf(d1, d1, acc);
+            } else {
+                acc = fmaf(q[2 * t], x0, acc);
+                acc = fmaf(q[2 * t + 1], x1, acc);
+            }
+        }
+    } else {
+#pragma unroll
+        for (int t = 0; t < 4; t++) {
+#pragma unroll
+            for (int h = 0; h < 2; h++) {
+                const __nv_fp8x2_storage_t pr = (__nv_fp8x2_storage_t)((w[t] >> (16 * h)) & 0xffffu);
+                const __half2_raw hr = __nv_cvt_fp8x2_to_halfraw2(pr, __NV_E4M3);
+                const float2 f = __half22float2(*reinterpret_cast<const __half2 *>(&hr));
+                acc = fmaf(q[4 * t + 2 * h], f.x, acc);
+                acc = fmaf(q[4 * t + 2 * h + 1], f.y, acc);
+            }
+        }
+    }
+}
+
+// Approximate distances of q to cid[0..nc) through the traversal rows; writes key(d~, id).
+template <int DT, int UN>
+__device__ __forceinline__ void eval_candidates_lp(const SearchArgs &a, const float (&qf)[16], float qn2,
+                                                   const uint32_t *cid, int nc, uint64_t *ckey) {
+    constexpr int E = DT == DT_BF16 ? 8 : 16;
+    constexpr int CH = 1;  // chunks per lane (lp_chunks <= 32)
+    const int lane = lane_id();
+    const int lpv = a.lp_lpv, sub = lane & (lpv - 1), grp = lane / lpv, ngrp = 32 / lpv;
+    const bool l2 = a.metric == MET_L2;
+    for (int c0 = 0; c0 < nc; c0 += ngrp * UN) {
+        uint4 v[UN][CH];
+        float2 inf[UN];
+#pragma unroll
+        for (int u = 0; u < UN; u++) {
+            const int c = c0 + grp + ngrp * u;
+            const uint32_t id = c < nc ? cid[c] : 0u;
+            const uint8_t *p = a.lp_vec + (size_t)id * a.lp_stride;
+#pragma unroll
+            for (int k = 0; k < CH; k++) {
+                const int ch = sub + k * lpv;
+                v[u][k] = (c < nc && ch < a.lp_chunks) ? ldg16(p + (size_t)ch * 16) : make_uint4(0, 0, 0, 0);
+            }
+            inf[u] = (DT == DT_FP8 && c < nc) ? __ldg(a.lp_info + id) : make_float2(1.f, 0.f);
+        }
+#pragma unroll
+        for (int u = 0; u < UN; u++) {
+            if (c0 + ngrp * u >= nc) break;  // warp-uniform
+            float s = 0.f;
+#pragma unroll
+            for (int k = 0; k < CH; k++) lp_chunk<DT>(v[u][k], qf + k * E, DT == DT_BF16 && l2, s);
+            s = group_sum(s, lpv);
+            float dist;
+            if (DT == DT_BF16) dist = l2 ? s : -s;
+            else dist = l2 ? (qn2 - 2.f * inf[u].x * s + inf[u].y) : -(inf[u].x * s);
+            const int c = c0 + grp + ngrp * u;
+            if (sub == 0 && c < nc) ckey[c] = make_key(dkey_f32(dist), cid[c]);
+        }
+    }
+}
+
+// Approximate distance to one point, every lane group gets the value.
+template <int DT>
+__device__ __forceinline__ uint32_t eval_one_lp(const SearchArgs &a, const float (&qf)[16], float qn2, uint32_t id) {
+    constexpr int E = DT == DT_BF16 ? 8 : 16;
+    constexpr int CH = 1;
+    const int sub = lane_id() & (a.lp_lpv - 1);
+    const bool l2 = a.metric == MET_L2;
+    const uint8_t *p = a.lp_vec + (size_t)id * a.lp_stride;
+    float s = 0.f;
+#pragma unroll
+    for (int k = 0; k < CH; k++) {
+        const int ch = sub + k * a.lp_lpv;
+        const uint4 v = ch < a.lp_chunks ? ldg16(p + (size_t)ch * 16) : make_uint4(0, 0, 0, 0);
+        lp_chunk<DT>(v, qf + k * E, DT == DT_BF16 && l2, s);
+    }
+    s = group_sum(s, a.lp_lpv);
+    if (DT == DT_BF16) return dkey_f32(l2 ? s : -s);
+    const float2 inf = __ldg(a.lp_info + id);
+    return dkey_f32(l2 ? (qn2 - 2.f * inf.x * s + inf.y) : -(inf.x * s));
+}
+
+// Key of r + slack: an approximate distance above it proves the exact one is above r.
+__device__ __forceinline__ uint32_t slack_key(const SearchArgs &a, uint32_t rk, float qn2) {
+    const float r = dval_f32(rk);
+    const float qn = sqrtf(qn2);
+    const float slack = a.rel_eps > 0.f ? a.rel_eps * fabsf(r) : (a.slackA * qn + a.slackB * qn2 + a.slackC);
+    return dkey_f32(r + slack);
+}
+
+// Sort keys[0..m) (shared or global memory) ascending with the warp: bitonic
+// network with flip stages, virtual +inf padding past m.
+__device__ __forceinline__ void warp_sort_keys(uint64_t *keys, int m) {
+    const int lane = lane_id();
+    int P = 1;
+    while (P < m) P <<= 1;
+    for (int k = 2; k <= P; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = lane; i < P / 2; i += 32) {
+                int lo, hi;
+                if (j == (k >> 1)) {
+                    const int blk = i / (k >> 1), off = i % (k >> 1);
+                    lo = blk * k + off;
+                    hi = blk * k + (k - 1 - off);
+                } else {
+                    const int blk = i / j, off = i % j;
+                    lo = blk * 2 * j + off;
+                    hi = lo + j;
+                }
+                if (hi < m) {
+                    const uint64_t x = keys[lo], y = keys[hi];
+                    if (y < x) {
+                        keys[lo] = y;
+                        keys[hi] = x;
+                    }
+                }
+            }
+            __syncwarp();
+        }
+    }
+}
+
+// The exact recheck of the precision form: keys[0..m) hold approximate keys
+// (visited bits ignored); replace them, in place, by the exact keys of the
+// points whose exact fp32 distance is <= r (rk), sorted by (dist, id).
+// cid/ckey are R-entry scratch.  Returns the count.  Whole warp.
+template <int CPL, int UN>
+__device__ int exact_filter_sort(const SearchArgs &a, int64_t qi, uint64_t *keys, int m, uint32_t rk, uint32_t *cid,
+                                 uint64_t *ckey, int R) {
+    const int lane = lane_id();
+    uint4 q32[CPL];
+    load_query<CPL>(a, a.queries + (size_t)qi * a.row_stride, q32);
+    int cnt = 0;
+    for (int base = 0; base < m; base += R) {
+        const int mm = min(R, m - base);
+        for (int t = lane; t < mm; t += 32) cid[t] = key_id(keys[base + t]);
+        __syncwarp();
+        eval_candidates<DT_F32, CPL, UN>(a, q32, cid, mm, ckey);
+        __syncwarp();
+        for (int t0 = 0; t0 < mm; t0 += 32) {
+            const int t = t0 + lane;
+            const uint64_t k = t < mm ? ckey[t] : kEmpty;
+            const bool in = t < mm && key_dk(k) <= rk;
+            const unsigned msk = __ballot_sync(0xffffffffu, in);
+            if (in) keys[cnt + __popc(msk & lanemask_lt())] = k;  // cnt <= base + t0: never ahead of the reads
+            cnt += __popc(msk);
+        }
+        __syncwarp();
+    }
+    warp_sort_keys(keys, cnt);
+    return cnt;
 }
 
 }  // namespace rr

@@ -75,6 +75,14 @@ struct rr_index {
     rr::Grow dbl_tmp;       // doubling: sort scratch of S u V
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};  // profile: start, beam, phase2, end
     rr_profile prof = {};
+    // low-precision traversal copies of an fp32 index (built on first use)
+    uint8_t *lp_bf16 = nullptr;
+    int32_t lp_bf16_stride = 0;
+    uint8_t *lp_fp8 = nullptr;
+    int32_t lp_fp8_stride = 0;
+    float2 *lp_fp8_info = nullptr;  // per row {scale, ||dequantised row||^2}
+    float *lp_stats = nullptr;      // device scratch for max ||x|| and max |x_i|
+    float max_norm = 0.f, max_abs = 0.f;
 };
 
 namespace rr {
@@ -111,7 +119,18 @@ struct SearchArgs {
     int32_t hash_lg;          // log2 of the beam kernel's seen-table slots (0 = library default)
     int32_t persistent;       // 1: resident grid, queries taken from *next_q (must start at 0)
     int32_t *next_q;
+    // low-precision traversal (fp32 indexes): vec/row_* above describe the exact fp32 rows
+    int32_t prec;             // RR_PREC_EXACT / BF16 / FP8
+    int32_t d;                // elements per vector
+    const uint8_t *lp_vec;    // traversal rows
+    int32_t lp_stride, lp_chunks, lp_lpv;
+    const float2 *lp_info;    // fp8: {scale, ||x||^2} per row
+    float slackA, slackB, slackC;  // |d - d~| <= A ||q|| + B ||q||^2 + C
+    float rel_eps;            // > 0: slack = rel_eps * |r| instead
 };
+
+rr_status ensure_lowp(rr_index *ix, int prec, cudaStream_t st);
+void slack_coefficients(const rr_index *ix, int prec, float *A, float *Bq, float *C);
 
 rr_status launch_beam(const SearchArgs &a, int warps_per_cta, cudaStream_t s, int dtype_code);
 int beam_hash_lg(int beam);

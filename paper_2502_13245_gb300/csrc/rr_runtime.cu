@@ -277,6 +277,10 @@ rr_status rr_free_index(rr_index *ix) {
     grow_free(ix->dbl_tmp);
     for (int k = 0; k < 4; k++)
         if (ix->ev[k]) cudaEventDestroy(ix->ev[k]);
+    if (ix->lp_bf16) cudaFree(ix->lp_bf16);
+    if (ix->lp_fp8) cudaFree(ix->lp_fp8);
+    if (ix->lp_fp8_info) cudaFree(ix->lp_fp8_info);
+    if (ix->lp_stats) cudaFree(ix->lp_stats);
     delete ix;
     return RR_OK;
 }

@@ -488,6 +488,27 @@ extern "C" rr_status rr_range_search(rr_index *ix, const void *queries, int64_t 
     a.hash_lg = P.seen_log2;
     a.persistent = P.persistent ? 1 : 0;
     a.next_q = a.p2_count + 2;  // zeroed with the other counters in stage()
+    a.d = ix->d;
+    a.prec = RR_PREC_EXACT;
+    if (P.precision != RR_PREC_EXACT) {
+        // precision form: traverse a BF16 / FP8 copy, decide membership in exact fp32
+        if ((s = ensure_lowp(ix, P.precision, S.st)) != RR_OK) return S.fail(s);
+        a.prec = P.precision;
+        a.lp_vec = P.precision == RR_PREC_BF16 ? ix->lp_bf16 : ix->lp_fp8;
+        a.lp_stride = P.precision == RR_PREC_BF16 ? ix->lp_bf16_stride : ix->lp_fp8_stride;
+        a.lp_chunks = a.lp_stride / 16;
+        if (a.lp_chunks > 32) {
+            set_error("rr_range_search: %s traversal supports d <= %d", P.precision == RR_PREC_BF16 ? "BF16" : "FP8",
+                      P.precision == RR_PREC_BF16 ? 256 : 512);
+            return S.fail(RR_EINVAL);
+        }
+        int lpv = 1;
+        while (lpv < a.lp_chunks) lpv <<= 1;
+        a.lp_lpv = lpv;
+        a.lp_info = ix->lp_fp8_info;
+        slack_coefficients(ix, P.precision, &a.slackA, &a.slackB, &a.slackC);
+        a.rel_eps = P.recheck_eps > 0.f ? P.recheck_eps : 0.f;
+    }
     a.phase2 = greedy ? 1 : (doubling ? 2 : 0);
     const bool prof = P.profile != 0;
     const int64_t l0 = launches_so_far();
