@@ -13,6 +13,7 @@ is the operating point.  A step is one rr_range_search over the whole batch
 (beam phase, early stop, phase 2, CSR assembly).
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+       python bench.py --serve 0.1,0.25,0.5 [--fixed VARIANT:BEAM]   (serving leg, its own JSON line)
 Under torchrun (N > 1) every rank runs the same per-GPU batch on its own GPU
 (weak scaling); rank 0 prints one JSON line.
 """
@@ -170,6 +171,111 @@ def run_reference(args, cfg, ds):
     print(json.dumps(line), flush=True)
 
 
+def run_serve(args, cfg, ds, rr, gi, stream, dev):
+    """Serving leg: open-loop Poisson arrivals of single queries (radii mixed r, 1.5r, 2r) into the
+    continuous-batching server; per offered rate, the achieved rate and submit-to-ready latency."""
+    import torch
+    f = (args.fixed or "greedy:192").split(":")
+    variant, beam = f[0], int(f[1])
+    vl, esr = (int(f[2]), float(f[3])) if len(f) > 3 else (20, 1.0)
+    base = dict(beam=beam, es_visit_limit=vl, es_radius_mode=1 if variant.endswith("_es") else 0,
+                es_radius=float(ds.radius) * esr)
+    nq = len(ds.Q)
+    rs = np.random.default_rng(11)
+    mult = rs.choice([1.0, 1.5, 2.0], nq)
+    radii = ds.radius * mult
+    if ds.X.dtype != np.float32:
+        radii = np.floor(radii)
+    # batch throughput of this form on the same radius mix: the scale of the offered rates
+    Qd = torch.from_numpy(ds.Q).to("cuda:%d" % dev)
+    p = rr.rr_params_init(**base)
+    for _ in range(3):
+        st, res = rr.rr_range_search(gi.h, Qd, radii, variant, p, stream=stream.cuda_stream, result_on_device=True)
+        rr.rr_result_free(res)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(5):
+        st, res = rr.rr_range_search(gi.h, Qd, radii, variant, p, stream=stream.cuda_stream, result_on_device=True)
+        rr.rr_result_free(res)
+    torch.cuda.synchronize()
+    batch_qps = 5 * nq / (time.perf_counter() - t0)
+    log("serve: batch throughput of %s b=%d on the radius mix: %.0f QPS" % (variant, beam, batch_qps))
+    rows = []
+    Qh = np.ascontiguousarray(ds.Q)
+    for frac in [float(x) for x in args.serve.split(",") if x]:
+        rate = frac * batch_qps
+        n_arr = int(rate * args.serve_secs)
+        gaps = rs.exponential(1.0 / rate, n_arr)
+        t_arr = np.cumsum(gaps)
+        pick = rs.integers(0, nq, n_arr)
+        srv = gi.serve(workers=args.serve_workers, max_batch=args.serve_max_batch, batch_wait_us=args.serve_wait_us,
+                       variant=variant, result_budget_bytes=1 << 32, **base)
+        subs = []
+        lock = threading.Condition()
+        done = {"gen": False}
+        lag = []
+        collected = [0, 0]
+
+        def collector():
+            k = 0
+            while True:
+                with lock:
+                    while k >= len(subs) and not done["gen"]:
+                        lock.wait(0.01)
+                    if k >= len(subs):
+                        return
+                    first, cnt = subs[k]
+                k += 1
+                while True:
+                    st, res = rr.rr_serve_collect(srv.h, first, cnt, 1000)
+                    if st == rr.RR_OK:
+                        collected[0] += cnt
+                        collected[1] += res.total
+                        rr.rr_result_free(res)
+                        break
+
+        th = threading.Thread(target=collector)
+        th.start()
+        rr.rr_serve_stats(srv.h, reset=True)
+        ts = time.perf_counter()
+        i = 0
+        while i < n_arr:
+            now = time.perf_counter() - ts
+            j = int(np.searchsorted(t_arr, now, side="right"))
+            if j > i:
+                idx = pick[i:j]
+                first = rr.rr_serve_submit(srv.h, Qh[idx], radii[idx])
+                lag.append(now - t_arr[i])
+                with lock:
+                    subs.append((first, j - i))
+                    lock.notify()
+                i = j
+            else:
+                time.sleep(max(0.0, min(2e-4, t_arr[i] - now)))
+        with lock:
+            done["gen"] = True
+            lock.notify()
+        th.join()
+        wall = time.perf_counter() - ts
+        sst = rr.rr_serve_stats(srv.h).as_dict()
+        srv.close()
+        row = {"offered_frac": frac, "offered_qps": rate, "achieved_qps": collected[0] / wall,
+               "p50_us": sst["p50_us"], "p99_us": sst["p99_us"], "mean_us": sst["mean_us"], "max_us": sst["max_us"],
+               "mean_batch": sst["mean_batch"], "batches": sst["batches"], "requests": collected[0],
+               "results": collected[1], "generator_lag_p99_us": float(np.percentile(lag, 99) * 1e6) if lag else 0.0}
+        rows.append(row)
+        log("serve: offered %.0f QPS (%.2f of batch) -> %.0f QPS, p50 %.0f us, p99 %.0f us, mean batch %.0f" % (
+            rate, frac, row["achieved_qps"], row["p50_us"], row["p99_us"], row["mean_batch"]))
+    line = {"metric": "serving latency under open-loop Poisson load", "unit": "us", "higher_is_better": False,
+            "value": rows[-1]["p99_us"] if rows else None, "n_gpus": 1, "dtype": str(ds.X.dtype), "data": "synthetic",
+            "config": {"workload": "%s: n=%d d=%d, single-query requests, radii r/1.5r/2r" % (cfg.name, cfg.n, cfg.d),
+                       "variant": variant, "beam": beam, "workers": args.serve_workers,
+                       "max_batch": args.serve_max_batch, "batch_wait_us": args.serve_wait_us,
+                       "seconds_per_rate": args.serve_secs, "batch_qps": batch_qps},
+            "rates": rows}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -186,6 +292,11 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--fixed", default="", help="VARIANT:BEAM[:VL:ESR] -- skip the sweep and time this form")
     ap.add_argument("--no-tune", action="store_true", help="keep the library's default launch shape")
+    ap.add_argument("--serve", default="", help="serving leg: offered rates as fractions of batch QPS, e.g. 0.1,0.5")
+    ap.add_argument("--serve-secs", type=float, default=3.0)
+    ap.add_argument("--serve-workers", type=int, default=3)
+    ap.add_argument("--serve-max-batch", type=int, default=4096)
+    ap.add_argument("--serve-wait-us", type=int, default=100)
     args = ap.parse_args()
 
     ws, rank, local = dist_env()
@@ -210,6 +321,10 @@ def main():
     sh = stream.cuda_stream
 
     gi = rr.Index.from_arrays(ds.X, ds.adj, ds.start, device=dev)
+    if args.serve:
+        if rank == 0:
+            run_serve(args, cfg, ds, rr, gi, stream, dev)
+        return
     Qd = torch.from_numpy(ds.Q).to("cuda:%d" % dev)
     nq = Qd.shape[0]
 

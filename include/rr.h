@@ -229,6 +229,69 @@ rr_status rr_beam_search_noalloc(rr_index *index, const void *queries, int64_t n
                                  const rr_params *params, void *stream, int32_t *out_counts, uint32_t *out_ids,
                                  void *out_dists);
 
+/* ---------------------------------------------------------------------------
+ * Serving: continuous batching of range queries that arrive one by one (the
+ * batched search of Alg. 6 / Alg. 3 run as a service).  `workers` host threads
+ * each own a CUDA stream and a scratch view of the index; each repeatedly
+ * forms a batch from everything queued (up to max_batch, waiting at most
+ * batch_wait_us for it to fill), searches it, and publishes per-request
+ * results, so requests that arrive while other batches are on the GPU are
+ * admitted into the next free worker and their work overlaps on the device.
+ * Admission is by result memory, because match counts are heavy-tailed: a
+ * request is admitted only while the bytes of results held (finished but not
+ * yet polled, plus reserve_per_request for each request in flight) stay
+ * within result_budget_bytes; one request is always admitted when nothing is
+ * held, so the server makes progress.  A batch's results are capped at what
+ * the budget has left (at least its reservation; each request's first beam of
+ * up to b results is always kept); a request whose results were cut carries
+ * RR_FLAG_TRUNCATED and holds a subset of its answer.
+ * Each request's result is the same as in any other batch (every query is
+ * searched independently).
+ * ------------------------------------------------------------------------- */
+typedef struct rr_server rr_server;
+
+typedef struct {
+    int32_t workers;             /* concurrent batches (default 2) */
+    int32_t max_batch;           /* requests per batch (default 4096) */
+    int32_t batch_wait_us;       /* wait for a batch to fill (default 200 us) */
+    int32_t variant;             /* rr_variant of every request (default RR_GREEDY_ES) */
+    rr_params params;            /* search parameters (rr_params_init defaults) */
+    int64_t result_budget_bytes; /* admission budget (default 4 GiB) */
+    int64_t reserve_per_request; /* bytes reserved per request in flight (0 = 8 * beam + 32) */
+} rr_serve_cfg;
+
+typedef struct {
+    int64_t submitted, completed, polled, queued, in_flight;
+    int64_t batches;
+    double mean_batch;           /* requests per batch */
+    double p50_us, p99_us, mean_us, max_us;  /* submit -> result ready, since the last reset */
+    double qps;                  /* completions per second since the last reset */
+    int64_t bytes_held;          /* result bytes held + reserved */
+    int64_t admission_waits;     /* times a worker stopped filling a batch for lack of budget */
+} rr_serve_stats_t;
+
+void rr_serve_cfg_init(rr_serve_cfg *cfg);
+/* Start a server on an index (the index must outlive it). */
+rr_status rr_serve_create(rr_index *index, const rr_serve_cfg *cfg, rr_server **out);
+/* Queue n requests: queries n x d in host memory (the index's element type),
+ * radii (n, host) or NULL for `radius`.  Tickets first_ticket .. first_ticket+n-1. */
+rr_status rr_serve_submit(rr_server *srv, const void *queries, int64_t n, const double *radii, double radius,
+                          uint64_t *first_ticket);
+/* Wait up to timeout_ms (0 = do not wait) for a ticket.  RR_OK: *out is that
+ * request's result (nq = 1, host memory, free with rr_result_free) and the
+ * ticket is retired; RR_EBUSY: still pending; RR_EINVAL: unknown or retired. */
+rr_status rr_serve_poll(rr_server *srv, uint64_t ticket, int32_t timeout_ms, rr_result *out);
+/* Wait up to timeout_ms for the n consecutive tickets first .. first+n-1 (as
+ * returned by one rr_serve_submit) and return their results as one CSR (nq =
+ * n, host memory, in ticket order), retiring them.  RR_EBUSY: not all done
+ * yet (nothing retired).  A request that failed is retired with an empty row
+ * and the call returns the first failure's status. */
+rr_status rr_serve_collect(rr_server *srv, uint64_t first, int64_t n, int32_t timeout_ms, rr_result *out);
+/* Counters and latency percentiles; reset = 1 starts a new measurement window. */
+rr_status rr_serve_stats(rr_server *srv, rr_serve_stats_t *out, int32_t reset);
+/* Stop the workers (queued requests are finished first) and free the server. */
+rr_status rr_serve_destroy(rr_server *srv);
+
 /* Free the arrays of a result (host or device) and zero the struct. */
 rr_status rr_result_free(rr_result *result);
 

@@ -32,7 +32,8 @@ RR_FLAG_TRUNCATED, RR_FLAG_EARLY_STOPPED, RR_FLAG_PHASE2 = 1, 2, 4
 # every symbol include/rr.h declares (checked by the ABI test)
 EXPORTS = ["rr_params_init", "rr_create_index", "rr_load_index", "rr_free_index", "rr_index_info_get",
            "rr_range_search", "rr_brute_force", "rr_result_free", "rr_last_error", "rr_last_profile",
-           "rr_beam_search_noalloc"]
+           "rr_beam_search_noalloc", "rr_serve_cfg_init", "rr_serve_create", "rr_serve_submit", "rr_serve_poll",
+           "rr_serve_collect", "rr_serve_stats", "rr_serve_destroy"]
 
 
 class RRError(RuntimeError):
@@ -53,6 +54,23 @@ class Profile(ctypes.Structure):
     _fields_ = [("beam_ms", ctypes.c_float), ("phase2_ms", ctypes.c_float), ("output_ms", ctypes.c_float),
                 ("total_ms", ctypes.c_float), ("launches", ctypes.c_int32), ("phase2_steps", ctypes.c_int32),
                 ("phase2_queries", ctypes.c_int32), ("valid", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class ServeCfg(ctypes.Structure):
+    _fields_ = [("workers", ctypes.c_int32), ("max_batch", ctypes.c_int32), ("batch_wait_us", ctypes.c_int32),
+                ("variant", ctypes.c_int32), ("params", Params), ("result_budget_bytes", ctypes.c_int64),
+                ("reserve_per_request", ctypes.c_int64)]
+
+
+class ServeStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("polled", ctypes.c_int64),
+                ("queued", ctypes.c_int64), ("in_flight", ctypes.c_int64), ("batches", ctypes.c_int64),
+                ("mean_batch", ctypes.c_double), ("p50_us", ctypes.c_double), ("p99_us", ctypes.c_double),
+                ("mean_us", ctypes.c_double), ("max_us", ctypes.c_double), ("qps", ctypes.c_double),
+                ("bytes_held", ctypes.c_int64), ("admission_waits", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -114,6 +132,20 @@ def load_library(path: str | None = None):
     L.rr_last_profile.argtypes = [P, P]
     L.rr_beam_search_noalloc.restype = ctypes.c_int
     L.rr_beam_search_noalloc.argtypes = [P, P, I64, D, I32, P, P, P, P, P]
+    L.rr_serve_cfg_init.restype = None
+    L.rr_serve_cfg_init.argtypes = [P]
+    L.rr_serve_create.restype = ctypes.c_int
+    L.rr_serve_create.argtypes = [P, P, P]
+    L.rr_serve_submit.restype = ctypes.c_int
+    L.rr_serve_submit.argtypes = [P, P, I64, P, D, P]
+    L.rr_serve_poll.restype = ctypes.c_int
+    L.rr_serve_poll.argtypes = [P, ctypes.c_uint64, I32, P]
+    L.rr_serve_collect.restype = ctypes.c_int
+    L.rr_serve_collect.argtypes = [P, ctypes.c_uint64, I64, I32, P]
+    L.rr_serve_stats.restype = ctypes.c_int
+    L.rr_serve_stats.argtypes = [P, P, I32]
+    L.rr_serve_destroy.restype = ctypes.c_int
+    L.rr_serve_destroy.argtypes = [P]
     _lib = L
     return L
 
@@ -263,6 +295,67 @@ def rr_result_free(res: Result):
     _check(load_library().rr_result_free(ctypes.byref(res)))
 
 
+def rr_serve_cfg_init(**overrides) -> ServeCfg:
+    c = ServeCfg()
+    load_library().rr_serve_cfg_init(ctypes.byref(c))
+    for k, v in overrides.items():
+        if k == "variant" and isinstance(v, str):
+            v = VARIANTS[v]
+        if hasattr(c, k):
+            setattr(c, k, v)
+        elif hasattr(c.params, k):
+            setattr(c.params, k, v)
+        else:
+            raise TypeError("unknown serving parameter %s" % k)
+    return c
+
+
+def rr_serve_create(handle, cfg: ServeCfg | None = None):
+    s = ctypes.c_void_p()
+    _check(load_library().rr_serve_create(handle, ctypes.byref(cfg) if cfg else None, ctypes.byref(s)))
+    return s
+
+
+def rr_serve_submit(server, queries, radius) -> int:
+    """Queue len(queries) requests (host array); returns the first ticket."""
+    qp, qdev, qk = _ptr_and_device(queries)
+    if qdev:
+        raise ValueError("rr_serve_submit takes host queries")
+    n = qk.shape[0]
+    rp, rs, rk = _radii(n, radius)
+    t = ctypes.c_uint64()
+    _check(load_library().rr_serve_submit(server, qp, n, rp, rs, ctypes.byref(t)))
+    return t.value
+
+
+def rr_serve_poll(server, ticket, timeout_ms=0):
+    """(status, Result): RR_OK with the request's result, or RR_EBUSY while pending."""
+    res = Result()
+    st = load_library().rr_serve_poll(server, ticket, int(timeout_ms), ctypes.byref(res))
+    if st not in (RR_OK, RR_EBUSY):
+        raise RRError(st, rr_last_error())
+    return st, res
+
+
+def rr_serve_collect(server, first, n, timeout_ms=0):
+    """(status, Result) for n consecutive tickets from `first`: RR_OK with one CSR, or RR_EBUSY."""
+    res = Result()
+    st = load_library().rr_serve_collect(server, int(first), int(n), int(timeout_ms), ctypes.byref(res))
+    if st not in (RR_OK, RR_EBUSY):
+        raise RRError(st, rr_last_error())
+    return st, res
+
+
+def rr_serve_stats(server, reset=False) -> ServeStats:
+    o = ServeStats()
+    _check(load_library().rr_serve_stats(server, ctypes.byref(o), 1 if reset else 0))
+    return o
+
+
+def rr_serve_destroy(server):
+    _check(load_library().rr_serve_destroy(server))
+
+
 # ------------------------------------------------------------------------------------------------
 # convenience
 # ------------------------------------------------------------------------------------------------
@@ -338,3 +431,48 @@ class Index:
 
     def brute_force(self, Q, radius, stream=None) -> RangeResult:
         return RangeResult(rr_brute_force(self.h, Q, radius, stream=stream))
+
+    def serve(self, **cfg) -> "Server":
+        return Server(self, rr_serve_cfg_init(**cfg))
+
+
+class Server:
+    """Continuous-batching server over an Index (rr_serve_*)."""
+
+    def __init__(self, index: Index, cfg: ServeCfg):
+        self.index = index  # keeps the index alive
+        self.h = rr_serve_create(index.h, cfg)
+
+    def submit(self, Q, radius) -> np.ndarray:
+        t0 = rr_serve_submit(self.h, Q, radius)
+        return np.arange(t0, t0 + len(Q), dtype=np.uint64)
+
+    def poll(self, ticket, timeout_ms=0):
+        """RangeResult of one request (nq = 1), or None while it is pending."""
+        st, res = rr_serve_poll(self.h, int(ticket), timeout_ms)
+        return RangeResult(res) if st == RR_OK else None
+
+    def collect(self, first, n, timeout_ms=0):
+        """RangeResult of the n requests first .. first+n-1 (one submit), or None while any is pending."""
+        st, res = rr_serve_collect(self.h, int(first), int(n), timeout_ms)
+        return RangeResult(res) if st == RR_OK else None
+
+    def stats(self, reset=False) -> dict:
+        return rr_serve_stats(self.h, reset).as_dict()
+
+    def close(self):
+        if self.h:
+            rr_serve_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

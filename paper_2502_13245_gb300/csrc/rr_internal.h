@@ -83,7 +83,14 @@ struct rr_index {
     float2 *lp_fp8_info = nullptr;  // per row {scale, ||dequantised row||^2}
     float *lp_stats = nullptr;      // device scratch for max ||x|| and max |x_i|
     float max_norm = 0.f, max_abs = 0.f;
+    // a worker view of another index: shares the vectors, adjacency and traversal copies
+    // (not freed with it) and owns its own scratch, so views can search concurrently
+    bool shared_data = false;
 };
+
+namespace rr {
+rr_index *index_worker_view(const rr_index *parent);
+}  // namespace rr
 
 namespace rr {
 

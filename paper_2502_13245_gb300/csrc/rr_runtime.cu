@@ -264,6 +264,13 @@ rr_status rr_load_index(const char *path, int32_t device, rr_index **out) {
 rr_status rr_free_index(rr_index *ix) {
     if (!ix) return RR_OK;
     DeviceGuard dg(ix->device);
+    if (ix->shared_data) {  // a worker view: the data belong to the parent index
+        ix->vec = nullptr;
+        ix->adj = nullptr;
+        ix->lp_bf16 = ix->lp_fp8 = nullptr;
+        ix->lp_fp8_info = nullptr;
+        ix->lp_stats = nullptr;
+    }
     if (ix->vec) cudaFree(ix->vec);
     if (ix->adj) cudaFree(ix->adj);
     if (ix->arena.base) cudaFree(ix->arena.base);
@@ -312,3 +319,16 @@ rr_status rr_result_free(rr_result *r) {
 
 }  // extern "C"
 
+namespace rr {
+rr_index *index_worker_view(const rr_index *p) {
+    rr_index *v = new (std::nothrow) rr_index();
+    if (!v) return nullptr;
+    v->n = p->n; v->d = p->d; v->dtype = p->dtype; v->metric = p->metric; v->R = p->R; v->start = p->start;
+    v->device = p->device; v->row_stride = p->row_stride; v->vec = p->vec; v->adj = p->adj;
+    v->lp_bf16 = p->lp_bf16; v->lp_bf16_stride = p->lp_bf16_stride;
+    v->lp_fp8 = p->lp_fp8; v->lp_fp8_stride = p->lp_fp8_stride; v->lp_fp8_info = p->lp_fp8_info;
+    v->lp_stats = p->lp_stats; v->max_norm = p->max_norm; v->max_abs = p->max_abs;
+    v->shared_data = true;
+    return v;
+}
+}  // namespace rr
