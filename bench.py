@@ -202,8 +202,10 @@ def run_serve(args, cfg, ds, rr, gi, stream, dev):
     log("serve: batch throughput of %s b=%d on the radius mix: %.0f QPS" % (variant, beam, batch_qps))
     rows = []
     Qh = np.ascontiguousarray(ds.Q)
-    for frac in [float(x) for x in args.serve.split(",") if x]:
-        rate = frac * batch_qps
+    for spec in [float(x) for x in args.serve.split(",") if x]:
+        # a value <= 1 is a fraction of the batch throughput, a larger one an absolute rate (QPS)
+        rate = spec * batch_qps if spec <= 1.0 else spec
+        frac = rate / batch_qps
         n_arr = int(rate * args.serve_secs)
         gaps = rs.exponential(1.0 / rate, n_arr)
         t_arr = np.cumsum(gaps)
@@ -292,7 +294,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--fixed", default="", help="VARIANT:BEAM[:VL:ESR] -- skip the sweep and time this form")
     ap.add_argument("--no-tune", action="store_true", help="keep the library's default launch shape")
-    ap.add_argument("--serve", default="", help="serving leg: offered rates as fractions of batch QPS, e.g. 0.1,0.5")
+    ap.add_argument("--serve", default="",
+                    help="serving leg: offered rates, fractions of batch QPS (<= 1) or QPS, e.g. 0.1,0.5 or 5000,20000")
     ap.add_argument("--serve-secs", type=float, default=3.0)
     ap.add_argument("--serve-workers", type=int, default=3)
     ap.add_argument("--serve-max-batch", type=int, default=4096)
@@ -320,6 +323,7 @@ def main():
     stream = torch.cuda.Stream()
     sh = stream.cuda_stream
 
+    torch.cuda.empty_cache()  # a radius picked in this process leaves torch's cache full
     gi = rr.Index.from_arrays(ds.X, ds.adj, ds.start, device=dev)
     if args.serve:
         if rank == 0:
@@ -404,8 +408,20 @@ def main():
 
     # exact counters of the chosen form -> algorithmic bytes (the beam phase alone: its own variant)
     beam_only = ("beam_es" if variant.endswith("_es") else "beam", form[1], form[2])
-    st_full = run_once(form, beam, stats=1).stats
-    st_beam = run_once(beam_only, beam, stats=1).stats
+
+    def stats_of(fm):
+        # exact counters keep one n-bit set per query: gather them over chunks of the batch
+        chunk = max(1, min(nq, (8 << 30) // max(1, (ds.X.shape[0] + 7) // 8)))
+        parts = []
+        for s0 in range(0, nq, chunk):
+            p = params(fm, beam, collect_stats=1)
+            st, res = rr.rr_range_search(gi.h, Qd[s0:s0 + chunk], ds.radius, fm[0], p, stream=sh,
+                                         result_on_device=False)
+            parts.append(rr.RangeResult(res, st).stats)
+        return np.concatenate(parts)
+
+    st_full = stats_of(form)
+    st_beam = stats_of(beam_only)
     row = ds.X.shape[1] * ds.X.dtype.itemsize
     R = ds.adj.shape[1]
     bytes_beam = int(st_beam["visits_beam"].sum()) * 4 * R + int(st_beam["distinct"].sum()) * row + nq * row

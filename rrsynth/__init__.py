@@ -121,11 +121,12 @@ def _family_sizes(rng, total, alpha, cap):
 
 
 def mixture_u8(n, d, n_centres, sigma, seed, dup_frac=0.2, fam_alpha=1.0, fam_cap=500, dup_sigma=2.0,
-               lo=40.0, hi=215.0, chunk=1 << 16):
+               lo=40.0, hi=215.0, chunk=1 << 16, streams=0):
     """uint8 Gaussian mixture with Zipf(1) weights and near-duplicate families.
 
     Returns (X uint8 [n,d], centres float64, weights).  Rows are shuffled so ids
-    carry no cluster order."""
+    carry no cluster order.  streams > 0 draws the noise of the base rows from
+    that many independent seeded streams (chunks of rows, in threads)."""
     rng = np.random.Generator(np.random.PCG64(seed))
     centres = rng.uniform(lo, hi, size=(n_centres, d))
     w = 1.0 / np.arange(1, n_centres + 1, dtype=np.float64)
@@ -135,10 +136,25 @@ def mixture_u8(n, d, n_centres, sigma, seed, dup_frac=0.2, fam_alpha=1.0, fam_ca
     n_base = n - n_dup
     X = np.empty((n, d), dtype=np.uint8)
     assign = rng.choice(n_centres, size=n_base, p=w)
-    for s in range(0, n_base, chunk):
-        e = min(n_base, s + chunk)
-        v = centres[assign[s:e]] + rng.normal(0.0, sigma, size=(e - s, d))
-        X[s:e] = np.clip(np.rint(v), 0, 255).astype(np.uint8)
+    if streams > 0:
+        import concurrent.futures as cf
+        kids = np.random.SeedSequence(seed).spawn(streams)
+        bounds = np.linspace(0, n_base, streams + 1).astype(np.int64)
+
+        def fill(j):
+            g = np.random.Generator(np.random.PCG64(kids[j]))
+            for s in range(int(bounds[j]), int(bounds[j + 1]), chunk):
+                e = min(int(bounds[j + 1]), s + chunk)
+                v = centres[assign[s:e]] + g.normal(0.0, sigma, size=(e - s, d))
+                X[s:e] = np.clip(np.rint(v), 0, 255).astype(np.uint8)
+
+        with cf.ThreadPoolExecutor(max_workers=min(streams, os.cpu_count() or 4)) as ex:
+            list(ex.map(fill, range(streams)))
+    else:
+        for s in range(0, n_base, chunk):
+            e = min(n_base, s + chunk)
+            v = centres[assign[s:e]] + rng.normal(0.0, sigma, size=(e - s, d))
+            X[s:e] = np.clip(np.rint(v), 0, 255).astype(np.uint8)
     if n_dup > 0:
         _grow_families(rng, X, n_base, sizes, dup_sigma, lambda v: np.clip(np.rint(v), 0, 255).astype(np.uint8))
     perm = rng.permutation(n)
@@ -228,6 +244,31 @@ def nn1_distances(X, Q, metric=M_L2, qblock=1024, xblock=1 << 16):
     return out
 
 
+def nn1_distances_exact(X, Q, qblock=512, xblock=1 << 20):
+    """Exact squared-L2 1-NN distance per query for 8-bit data (torch; a CUDA device when present).
+
+    Products of 8-bit values are exact in TF32 and fp32, and their sums (< 2^24
+    for d <= 256) exact in any order; the distance is formed from them in int64."""
+    import torch
+    dev = torch.device("cuda" if torch.cuda.is_available() else "cpu")
+    prev = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = True
+    try:
+        Qf = torch.from_numpy(np.ascontiguousarray(Q)).to(dev).float()
+        nq = (Qf * Qf).sum(1).to(torch.int64)
+        best = torch.full((Q.shape[0],), np.iinfo(np.int64).max, dtype=torch.int64, device=dev)
+        for xs in range(0, X.shape[0], xblock):
+            Xb = torch.from_numpy(np.ascontiguousarray(X[xs:xs + xblock])).to(dev).float()
+            nx = (Xb * Xb).sum(1).to(torch.int64)
+            for s in range(0, Q.shape[0], qblock):
+                G = (Qf[s:s + qblock] @ Xb.T).to(torch.int64)
+                D = nq[s:s + qblock, None] + nx[None, :] - 2 * G
+                best[s:s + qblock] = torch.minimum(best[s:s + qblock], D.min(1).values)
+        return best.cpu().numpy()
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = prev
+
+
 def pick_radius(nn1, zero_frac=0.6):
     """Radius at the (1 - zero_frac) quantile of 1-NN distances (lower order statistic)."""
     srt = np.sort(nn1)
@@ -258,6 +299,7 @@ class Config:
     seed: int
     near_sigma: float
     zero_frac: float = 0.6
+    streams: int = 0           # > 0: base rows drawn from that many seeded streams in parallel
 
 
 CONFIGS = {
@@ -267,6 +309,10 @@ CONFIGS = {
     "c1": Config("c1", 1_000_000, 128, 10_000, "u8", M_L2, 1000, 12.0, 5000, 64, 128, 1.2, 2, 1, 2.0),
     # 1,000,000 x 200 fp32 unit vectors, inner product, 10,000 queries, R=64 L=128 alpha=1.0
     "c2": Config("c2", 1_000_000, 200, 10_000, "f32", M_IP, 1000, 0.06, 5000, 64, 128, 1.0, 1, 2, 0.01),
+    # 10,000,000 x 256 uint8, 5,000 centres, families up to 20,000, 100,000 queries, R=64 L=48 alpha=1.2,
+    # one construction pass (minutes on the host's cores instead of the better part of an hour for two)
+    "c3": Config("c3", 10_000_000, 256, 100_000, "u8", M_L2, 5000, 12.0, 20000, 64, 48, 1.2, 1, 3, 2.0,
+                 streams=64),
 }
 
 
@@ -312,7 +358,8 @@ def make_dataset(cfg: Config, cache_dir: str | None = None, threads: int = 0, ve
             return Dataset(cfg, z["X"], z["Q"], z["adj"], int(z["start"]), z["radius"].item(), 0.0)
     t0 = time.time()
     if cfg.dtype == "u8":
-        X, C, w = mixture_u8(cfg.n, cfg.d, cfg.n_centres, cfg.sigma, cfg.seed, fam_cap=cfg.fam_cap)
+        X, C, w = mixture_u8(cfg.n, cfg.d, cfg.n_centres, cfg.sigma, cfg.seed, fam_cap=cfg.fam_cap,
+                             streams=cfg.streams)
         Q = queries_u8(X, C, w, cfg.nq, cfg.sigma, cfg.seed + 1, near_sigma=cfg.near_sigma)
     else:
         X, C, w = vmf_f32(cfg.n, cfg.d, cfg.n_centres, cfg.sigma, cfg.seed, fam_cap=cfg.fam_cap)
@@ -320,7 +367,10 @@ def make_dataset(cfg: Config, cache_dir: str | None = None, threads: int = 0, ve
     t1 = time.time()
     # the radius comes from the 1-NN distances of (at most) 2,000 seeded queries
     sub = Q if cfg.nq <= 2000 else Q[np.random.Generator(np.random.PCG64(cfg.seed + 7)).choice(cfg.nq, 2000, replace=False)]
-    nn1 = nn1_distances(X, sub, cfg.metric)
+    if cfg.dtype == "u8" and cfg.d > 128:
+        nn1 = nn1_distances_exact(X, sub)  # fp32 forms of ||x||^2 - 2<x,q> would round above d = 128
+    else:
+        nn1 = nn1_distances(X, sub, cfg.metric)
     radius = pick_radius(nn1, cfg.zero_frac)
     radius = int(radius) if cfg.dtype == "u8" else float(radius)
     t2 = time.time()
