@@ -147,7 +147,7 @@ def run_reference(args, cfg, ds):
     ws, rank, _ = dist_env()
     if rank != 0:
         return
-    oi = oracle.Index(ds.X, ds.adj, ds.start)
+    oi = oracle.Index(ds.X, ds.adj, ds.start, metric=oracle.IP if cfg.metric == rrsynth.M_IP else oracle.L2)
     variant, beam = args.ref_variant, args.ref_beam
     cores = os.cpu_count() or 1
     sample = args.ref_sample
@@ -163,7 +163,8 @@ def run_reference(args, cfg, ds):
             "warmup": args.warmup, "ms_per_step": 1000 * dt / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
             "impl": "reference",
-            "config": {"workload": cfg.name + ": n=%d d=%d uint8, nq=%d, R=%d" % (cfg.n, cfg.d, cfg.nq, cfg.R),
+            "config": {"workload": cfg.name + ": n=%d d=%d %s, nq=%d, R=%d" % (
+                cfg.n, cfg.d, "uint8" if cfg.dtype == "u8" else "fp32", cfg.nq, cfg.R),
                        "variant": variant, "beam": beam},
             "cpu_baseline": {"value": qps, "unit": "queries/s", "cores": cores, "kind": "oracle",
                              "sample": "first %d of the %d queries per step, %s b=%d" % (sample, cfg.nq, variant, beam)},
@@ -294,6 +295,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--fixed", default="", help="VARIANT:BEAM[:VL:ESR] -- skip the sweep and time this form")
     ap.add_argument("--no-tune", action="store_true", help="keep the library's default launch shape")
+    ap.add_argument("--precision", type=int, default=0, choices=[0, 1, 2],
+                    help="fp32 indexes: 0 exact, 1 BF16 traversal, 2 FP8-e4m3 traversal (exact fp32 recheck)")
     ap.add_argument("--serve", default="",
                     help="serving leg: offered rates, fractions of batch QPS (<= 1) or QPS, e.g. 0.1,0.5 or 5000,20000")
     ap.add_argument("--serve-secs", type=float, default=3.0)
@@ -324,7 +327,8 @@ def main():
     sh = stream.cuda_stream
 
     torch.cuda.empty_cache()  # a radius picked in this process leaves torch's cache full
-    gi = rr.Index.from_arrays(ds.X, ds.adj, ds.start, device=dev)
+    metric = rr.RR_IP if cfg.metric == rrsynth.M_IP else rr.RR_L2
+    gi = rr.Index.from_arrays(ds.X, ds.adj, ds.start, metric=metric, device=dev)
     if args.serve:
         if rank == 0:
             run_serve(args, cfg, ds, rr, gi, stream, dev)
@@ -343,7 +347,7 @@ def main():
     def params(form, beam, **kw):
         variant, vl, esr = form
         return rr.rr_params_init(beam=beam, es_visit_limit=vl, es_radius_mode=1, es_radius=float(ds.radius) * esr,
-                                 **kw)
+                                 precision=args.precision, **kw)
 
     def run_once(form, beam, profile=0, stats=0):
         p = params(form, beam, profile=profile, collect_stats=stats)
@@ -422,7 +426,10 @@ def main():
 
     st_full = stats_of(form)
     st_beam = stats_of(beam_only)
-    row = ds.X.shape[1] * ds.X.dtype.itemsize
+    # bytes a distance evaluation gathers: the traversal row (fp32 / BF16 / FP8 + its scale and norm);
+    # the exact fp32 rechecks of the precision form come on top and are not counted
+    row = ds.X.shape[1] * (ds.X.dtype.itemsize if args.precision == 0 else (2 if args.precision == 1 else 1))
+    row += 8 if args.precision == 2 else 0
     R = ds.adj.shape[1]
     bytes_beam = int(st_beam["visits_beam"].sum()) * 4 * R + int(st_beam["distinct"].sum()) * row + nq * row
     bytes_all = (int(st_full["visits_beam"].sum()) + int(st_full["visits_phase2"].sum())) * 4 * R + \
@@ -490,7 +497,7 @@ def main():
     cpu = None
     if rank == 0 and not args.no_cpu:
         import oracle
-        oi = oracle.Index(ds.X, ds.adj, ds.start)
+        oi = oracle.Index(ds.X, ds.adj, ds.start, metric=oracle.IP if cfg.metric == rrsynth.M_IP else oracle.L2)
         cores = os.cpu_count() or 1
         sample = args.cpu_sample or 200
         tc = time.perf_counter()
@@ -504,9 +511,13 @@ def main():
         line = {
             "metric": "range QPS at AP>=0.95", "value": value, "unit": "queries/s", "n_gpus": ws,
             "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": step_ms, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
-            "config": {"workload": "%s: n=%d d=%d uint8 L2, nq=%d per GPU, Vamana R=%d L=%d alpha=%.2f" % (
-                cfg.name, cfg.n, cfg.d, cfg.nq, cfg.R, cfg.L_build, cfg.alpha),
+            "scaling": "weak", "vs_baseline": None, "data": "synthetic",
+            "dtype": "u8" if ds.X.dtype == np.uint8 else ["f32", "bf16+f32", "fp8+f32"][args.precision],
+            "config": {"workload": "%s: n=%d d=%d %s %s, nq=%d per GPU, Vamana R=%d L=%d alpha=%.2f" % (
+                cfg.name, cfg.n, cfg.d, "uint8" if ds.X.dtype == np.uint8 else "fp32",
+                "IP" if cfg.metric == rrsynth.M_IP else "L2", cfg.nq, cfg.R, cfg.L_build, cfg.alpha),
+                "precision": ["exact", "bf16 traversal, exact fp32 recheck", "fp8-e4m3 traversal, exact fp32 recheck"][
+                    args.precision],
                 "variant": variant, "beam": beam, "ap": best["ap"], "es_vl": form[1], "es_radius_over_r": form[2],
                 "launch_shape": tuned or "library default",
                 "beam_phase_evals_per_distinct": float(st_beam["evals"].sum()) / max(1, int(st_beam["distinct"].sum())),
