@@ -41,6 +41,9 @@ VARIANTS = ["greedy", "greedy_es", "doubling", "doubling_es", "beam", "beam_es"]
 # Alg. 5 thresholds swept for the early-stopping variants: (vl, esr / r)
 ES_GRID = [(20, 1.0), (50, 1.5), (100, 2.0)]
 AP_TARGET = 0.95
+# DRAM bytes (read + write) of one beam-kernel launch from an ncu capture of the current kernel
+# (profiles/beam_kernel_c1_b192.md), keyed by (workload, variant, b); cleared whenever the kernel changes
+MEASURED_TRAFFIC = {("c1", "greedy", 192): 1.030496e9 + 4.459776e6}
 
 
 def log(*a):
@@ -526,7 +529,8 @@ def main():
                 "l2_policy": "index (vectors + adjacency %.0f MB) larger than L2" % (
                     (ds.X.nbytes + ds.adj.nbytes) / 1e6)},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                         "frac": achieved / hbm, "traffic": None, "kernel": "beam phase (Alg. 1 + Alg. 5)",
+                         "frac": achieved / hbm,
+                         "traffic": MEASURED_TRAFFIC.get((cfg.name, variant, beam)), "kernel": "beam phase (Alg. 1 + Alg. 5)",
                          "peak_kind": peak_kind, "whole_step_gbs": whole},
             "e2e": {"value": ws * nq / (e2e_ms / 1000.0), "unit": "queries/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
