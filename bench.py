@@ -357,8 +357,10 @@ def main():
         st, res = rr.rr_range_search(gi.h, Qd, ds.radius, form[0], p, stream=sh, result_on_device=False)
         return rr.RangeResult(res, st)
 
-    def time_form(form, beam, reps=3):
+    def time_form(form, beam, reps=3, base=None):
         p = params(form, beam)
+        for k, v in (base or {}).items():
+            setattr(p, k, v)
         variant = form[0]
         with torch.cuda.stream(stream):
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -479,6 +481,10 @@ def main():
     clocks = clk.summary()
     value = ws * nq / (step_ms / 1000.0)
 
+    # the same form in the plain launch: one warp per query over a full grid, library default shape,
+    # exact arithmetic (the chosen form's batching and precision choices switched off)
+    plain_ms = time_form(form, beam, reps=max(3, min(args.steps, 20)), base={"precision": 0})
+
     # end to end through the public API with host buffers: pinned queries in, host CSR out
     Qh = torch.from_numpy(ds.Q).pin_memory()
     h2d = int(Qh.numel() * Qh.element_size())
@@ -523,6 +529,9 @@ def main():
                     args.precision],
                 "variant": variant, "beam": beam, "ap": best["ap"], "es_vl": form[1], "es_radius_over_r": form[2],
                 "launch_shape": tuned or "library default",
+                "plain_launch": {"what": "same variant and b, one warp per query, default shape, exact",
+                                 "ms_per_step": plain_ms, "qps": ws * nq / (plain_ms / 1000.0),
+                                 "chosen_over_plain": plain_ms / step_ms},
                 "beam_phase_evals_per_distinct": float(st_beam["evals"].sum()) / max(1, int(st_beam["distinct"].sum())),
                 "plain_beam_form": None if plain_best is None else {
                     "beam": plain_best["beam"], "qps": plain_best["qps"], "ap": plain_best["ap"]},
