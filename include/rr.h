@@ -74,7 +74,8 @@ typedef enum { RR_PREC_EXACT = 0, RR_PREC_BF16 = 1, RR_PREC_FP8 = 2 } rr_precisi
 enum {
     RR_FLAG_TRUNCATED = 1,     /* doubling hit b_max, or results hit max_results_total */
     RR_FLAG_EARLY_STOPPED = 2, /* Alg. 5 ended the first beam search */
-    RR_FLAG_PHASE2 = 4         /* the greedy or doubling phase ran */
+    RR_FLAG_PHASE2 = 4,        /* the greedy or doubling phase ran */
+    RR_FLAG_CANCELED = 8       /* serving: dropped by rr_serve_cancel before it was searched */
 };
 
 typedef struct rr_index rr_index;
@@ -134,9 +135,9 @@ void rr_params_init(rr_params *p);
  *   vectors    n x d row-major, element type dtype
  *   adjacency  n x R uint32 row-major; 0xFFFFFFFF pads rows of degree < R
  *   start      entry point of every search (the medoid), 0 <= start < n
- * Requirements: 1 <= n < 2^31, 1 <= d <= 512 (8-bit) or 128 (fp32... see
- * rr_index_info for the accepted maximum), 1 <= R <= 128, every non-padding
- * adjacency entry < n.  Adjacency entries are not validated on the device;
+ * Requirements: 1 <= n < 2^31, 1 <= d <= 512 (any element type; the BF16
+ * traversal of the precision form takes d <= 256), 1 <= R <= 128, every
+ * non-padding adjacency entry < n.  Adjacency entries are not validated on the device;
  * invalid ids give RR_EINVAL when validate != 0 (a host-side scan). */
 rr_status rr_create_index(const void *vectors, int64_t n, int32_t d, int32_t dtype, int32_t metric,
                           const uint32_t *adjacency, int32_t R, int64_t start, int32_t device,
@@ -234,14 +235,20 @@ rr_status rr_beam_search_noalloc(rr_index *index, const void *queries, int64_t n
  * batched search of Alg. 6 / Alg. 3 run as a service).  `workers` host threads
  * each own a CUDA stream and a scratch view of the index; each repeatedly
  * forms a batch from everything queued (up to max_batch, waiting at most
- * batch_wait_us for it to fill), searches it, and publishes per-request
+ * batch_wait_us for it to fill), searches it, and publishes the requests'
  * results, so requests that arrive while other batches are on the GPU are
  * admitted into the next free worker and their work overlaps on the device.
+ * A batch's CSR stays in host memory, or in device memory when
+ * result_on_device = 1, until its requests are collected; each request's row
+ * is copied out once, by rr_serve_poll / rr_serve_collect (a gather kernel for
+ * device results).
  * Admission is by result memory, because match counts are heavy-tailed: a
  * request is admitted only while the bytes of results held (finished but not
- * yet polled, plus reserve_per_request for each request in flight) stay
- * within result_budget_bytes; one request is always admitted when nothing is
- * held, so the server makes progress.  A batch's results are capped at what
+ * yet collected, plus a reservation for each request in flight) stay within
+ * result_budget_bytes; one request is always admitted when nothing is held,
+ * so the server makes progress.  The reservation is reserve_per_request, or
+ * (0, the default) a running mean of the bytes requests have turned out to
+ * hold, never below 8 * beam + 32.  A batch's results are capped at what
  * the budget has left (at least its reservation; each request's first beam of
  * up to b results is always kept); a request whose results were cut carries
  * RR_FLAG_TRUNCATED and holds a subset of its answer.
@@ -257,7 +264,9 @@ typedef struct {
     int32_t variant;             /* rr_variant of every request (default RR_GREEDY_ES) */
     rr_params params;            /* search parameters (rr_params_init defaults) */
     int64_t result_budget_bytes; /* admission budget (default 4 GiB) */
-    int64_t reserve_per_request; /* bytes reserved per request in flight (0 = 8 * beam + 32) */
+    int64_t reserve_per_request; /* bytes reserved per request in flight (0 = running mean, see above) */
+    int32_t result_on_device;    /* 1: results in device memory (on the device the index lives on) */
+    int32_t reserved_cfg[3];
 } rr_serve_cfg;
 
 typedef struct {
@@ -268,6 +277,8 @@ typedef struct {
     double qps;                  /* completions per second since the last reset */
     int64_t bytes_held;          /* result bytes held + reserved */
     int64_t admission_waits;     /* times a worker stopped filling a batch for lack of budget */
+    int64_t canceled;            /* requests dropped by rr_serve_cancel */
+    int64_t reserve_per_request; /* the current reservation per admitted request (bytes) */
 } rr_serve_stats_t;
 
 void rr_serve_cfg_init(rr_serve_cfg *cfg);
@@ -278,19 +289,34 @@ rr_status rr_serve_create(rr_index *index, const rr_serve_cfg *cfg, rr_server **
 rr_status rr_serve_submit(rr_server *srv, const void *queries, int64_t n, const double *radii, double radius,
                           uint64_t *first_ticket);
 /* Wait up to timeout_ms (0 = do not wait) for a ticket.  RR_OK: *out is that
- * request's result (nq = 1, host memory, free with rr_result_free) and the
- * ticket is retired; RR_EBUSY: still pending; RR_EINVAL: unknown or retired. */
+ * request's result (nq = 1, host memory -- device memory with
+ * result_on_device -- free with rr_result_free) and the ticket is retired;
+ * RR_EBUSY: still pending (nothing allocated); RR_EINVAL: unknown or retired.
+ * A request whose search failed is retired with an empty row: *out is
+ * allocated all the same and the call returns the search's status. */
 rr_status rr_serve_poll(rr_server *srv, uint64_t ticket, int32_t timeout_ms, rr_result *out);
 /* Wait up to timeout_ms for the n consecutive tickets first .. first+n-1 (as
  * returned by one rr_serve_submit) and return their results as one CSR (nq =
- * n, host memory, in ticket order), retiring them.  RR_EBUSY: not all done
- * yet (nothing retired).  A request that failed is retired with an empty row
- * and the call returns the first failure's status. */
+ * n, in ticket order; host memory, or device memory with result_on_device,
+ * complete when the call returns), retiring them.  RR_EBUSY: not all done yet
+ * (nothing retired, nothing allocated).  A request that failed is retired with
+ * an empty row; *out is allocated all the same and the call returns the first
+ * failure's status. */
 rr_status rr_serve_collect(rr_server *srv, uint64_t first, int64_t n, int32_t timeout_ms, rr_result *out);
+/* Drop every request still queued (those in flight finish): each is retired
+ * as done with an empty row flagged RR_FLAG_CANCELED, to be collected as
+ * usual.  Returns how many were dropped.  For shedding load, and for ending a
+ * measurement window under overload. */
+int64_t rr_serve_cancel(rr_server *srv);
 /* Counters and latency percentiles; reset = 1 starts a new measurement window. */
 rr_status rr_serve_stats(rr_server *srv, rr_serve_stats_t *out, int32_t reset);
 /* Stop the workers (queued requests are finished first) and free the server. */
 rr_status rr_serve_destroy(rr_server *srv);
+
+/* Copy a result into host memory: *host becomes a host result with the same
+ * content (free with rr_result_free); a host result is copied as it is.
+ * Waits for the stream a device result is ordered on. */
+rr_status rr_result_to_host(const rr_result *result, rr_result *host);
 
 /* Free the arrays of a result (host or device) and zero the struct. */
 rr_status rr_result_free(rr_result *result);

@@ -27,13 +27,13 @@ VARIANTS = {"beam": RR_BEAM, "beam_es": RR_BEAM_ES, "doubling": RR_DOUBLING, "do
 RR_U8, RR_I8, RR_F32 = 0, 1, 2
 RR_L2, RR_IP = 0, 1
 RR_PREC_EXACT, RR_PREC_BF16, RR_PREC_FP8 = 0, 1, 2
-RR_FLAG_TRUNCATED, RR_FLAG_EARLY_STOPPED, RR_FLAG_PHASE2 = 1, 2, 4
+RR_FLAG_TRUNCATED, RR_FLAG_EARLY_STOPPED, RR_FLAG_PHASE2, RR_FLAG_CANCELED = 1, 2, 4, 8
 
 # every symbol include/rr.h declares (checked by the ABI test)
 EXPORTS = ["rr_params_init", "rr_create_index", "rr_load_index", "rr_free_index", "rr_index_info_get",
            "rr_range_search", "rr_brute_force", "rr_result_free", "rr_last_error", "rr_last_profile",
            "rr_beam_search_noalloc", "rr_serve_cfg_init", "rr_serve_create", "rr_serve_submit", "rr_serve_poll",
-           "rr_serve_collect", "rr_serve_stats", "rr_serve_destroy"]
+           "rr_serve_collect", "rr_serve_cancel", "rr_serve_stats", "rr_serve_destroy", "rr_result_to_host"]
 
 
 class RRError(RuntimeError):
@@ -62,7 +62,8 @@ class Profile(ctypes.Structure):
 class ServeCfg(ctypes.Structure):
     _fields_ = [("workers", ctypes.c_int32), ("max_batch", ctypes.c_int32), ("batch_wait_us", ctypes.c_int32),
                 ("variant", ctypes.c_int32), ("params", Params), ("result_budget_bytes", ctypes.c_int64),
-                ("reserve_per_request", ctypes.c_int64)]
+                ("reserve_per_request", ctypes.c_int64), ("result_on_device", ctypes.c_int32),
+                ("reserved_cfg", ctypes.c_int32 * 3)]
 
 
 class ServeStats(ctypes.Structure):
@@ -70,7 +71,8 @@ class ServeStats(ctypes.Structure):
                 ("queued", ctypes.c_int64), ("in_flight", ctypes.c_int64), ("batches", ctypes.c_int64),
                 ("mean_batch", ctypes.c_double), ("p50_us", ctypes.c_double), ("p99_us", ctypes.c_double),
                 ("mean_us", ctypes.c_double), ("max_us", ctypes.c_double), ("qps", ctypes.c_double),
-                ("bytes_held", ctypes.c_int64), ("admission_waits", ctypes.c_int64)]
+                ("bytes_held", ctypes.c_int64), ("admission_waits", ctypes.c_int64), ("canceled", ctypes.c_int64),
+                ("reserve_per_request", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -142,6 +144,10 @@ def load_library(path: str | None = None):
     L.rr_serve_poll.argtypes = [P, ctypes.c_uint64, I32, P]
     L.rr_serve_collect.restype = ctypes.c_int
     L.rr_serve_collect.argtypes = [P, ctypes.c_uint64, I64, I32, P]
+    L.rr_serve_cancel.restype = ctypes.c_int64
+    L.rr_serve_cancel.argtypes = [P]
+    L.rr_result_to_host.restype = ctypes.c_int
+    L.rr_result_to_host.argtypes = [P, P]
     L.rr_serve_stats.restype = ctypes.c_int
     L.rr_serve_stats.argtypes = [P, P, I32]
     L.rr_serve_destroy.restype = ctypes.c_int
@@ -333,7 +339,10 @@ def rr_serve_poll(server, ticket, timeout_ms=0):
     res = Result()
     st = load_library().rr_serve_poll(server, ticket, int(timeout_ms), ctypes.byref(res))
     if st not in (RR_OK, RR_EBUSY):
-        raise RRError(st, rr_last_error())
+        msg = rr_last_error()
+        if res.offsets:
+            rr_result_free(res)
+        raise RRError(st, msg)
     return st, res
 
 
@@ -342,8 +351,23 @@ def rr_serve_collect(server, first, n, timeout_ms=0):
     res = Result()
     st = load_library().rr_serve_collect(server, int(first), int(n), int(timeout_ms), ctypes.byref(res))
     if st not in (RR_OK, RR_EBUSY):
-        raise RRError(st, rr_last_error())
+        msg = rr_last_error()
+        if res.offsets:
+            rr_result_free(res)
+        raise RRError(st, msg)
     return st, res
+
+
+def rr_serve_cancel(server) -> int:
+    """Drop every queued request (retired with RR_FLAG_CANCELED); returns how many."""
+    return int(load_library().rr_serve_cancel(server))
+
+
+def rr_result_to_host(res: Result) -> Result:
+    """A host copy of a (host or device) result; free both with rr_result_free."""
+    h = Result()
+    _check(load_library().rr_result_to_host(ctypes.byref(res), ctypes.byref(h)))
+    return h
 
 
 def rr_serve_stats(server, reset=False) -> ServeStats:
@@ -447,15 +471,25 @@ class Server:
         t0 = rr_serve_submit(self.h, Q, radius)
         return np.arange(t0, t0 + len(Q), dtype=np.uint64)
 
+    def _wrap(self, res):
+        if res.on_device:  # a host copy for Python; the device arrays are freed here
+            h = rr_result_to_host(res)
+            rr_result_free(res)
+            res = h
+        return RangeResult(res)
+
     def poll(self, ticket, timeout_ms=0):
         """RangeResult of one request (nq = 1), or None while it is pending."""
         st, res = rr_serve_poll(self.h, int(ticket), timeout_ms)
-        return RangeResult(res) if st == RR_OK else None
+        return self._wrap(res) if st == RR_OK else None
 
     def collect(self, first, n, timeout_ms=0):
         """RangeResult of the n requests first .. first+n-1 (one submit), or None while any is pending."""
         st, res = rr_serve_collect(self.h, int(first), int(n), timeout_ms)
-        return RangeResult(res) if st == RR_OK else None
+        return self._wrap(res) if st == RR_OK else None
+
+    def cancel(self) -> int:
+        return rr_serve_cancel(self.h)
 
     def stats(self, reset=False) -> dict:
         return rr_serve_stats(self.h, reset).as_dict()

@@ -300,6 +300,43 @@ rr_status rr_index_info_get(const rr_index *ix, rr_index_info *info) {
     return RR_OK;
 }
 
+rr_status rr_result_to_host(const rr_result *r, rr_result *h) {
+    if (!r || !h) { set_error("rr_result_to_host: NULL argument"); return RR_EINVAL; }
+    memset(h, 0, sizeof *h);
+    const int64_t nq = r->nq, tot = r->total;
+    h->nq = nq;
+    h->total = tot;
+    h->dist_dtype = r->dist_dtype;
+    h->offsets = (int64_t *)malloc((size_t)(nq + 1) * 8);
+    h->ids = (uint32_t *)malloc((size_t)std::max<int64_t>(tot, 1) * 4);
+    h->dists = malloc((size_t)std::max<int64_t>(tot, 1) * 4);
+    h->flags = (uint8_t *)malloc((size_t)std::max<int64_t>(nq, 1));
+    if (r->stats) h->stats = (rr_query_stats *)malloc((size_t)std::max<int64_t>(nq, 1) * sizeof(rr_query_stats));
+    if (!h->offsets || !h->ids || !h->dists || !h->flags || (r->stats && !h->stats)) {
+        rr_result_free(h);
+        set_error("rr_result_to_host: allocation failed");
+        return RR_ENOMEM;
+    }
+    struct { void *dst; const void *src; size_t bytes; } parts[5] = {
+        {h->offsets, r->offsets, (size_t)(nq + 1) * 8}, {h->ids, r->ids, (size_t)tot * 4},
+        {h->dists, r->dists, (size_t)tot * 4}, {h->flags, r->flags, (size_t)nq},
+        {h->stats, r->stats, r->stats ? (size_t)nq * sizeof(rr_query_stats) : 0}};
+    if (!r->on_device) {
+        for (auto &p : parts)
+            if (p.bytes) memcpy(p.dst, p.src, p.bytes);
+        return RR_OK;
+    }
+    DeviceGuard dg(r->_device);
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)r->_stream);
+    for (auto &p : parts)
+        if (e == cudaSuccess && p.bytes) e = cudaMemcpy(p.dst, p.src, p.bytes, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) {
+        rr_result_free(h);
+        return cuda_fail(e, "rr_result_to_host");
+    }
+    return RR_OK;
+}
+
 rr_status rr_result_free(rr_result *r) {
     if (!r) return RR_OK;
     if (r->on_device) {

@@ -3,11 +3,14 @@
 // The paper evaluates batched search (Sec. 4); a service sees queries one at a
 // time.  Worker threads turn the arrival stream into batches: each owns a CUDA
 // stream and a scratch view of the index (shared vectors and graph), takes
-// whatever is queued when it becomes free, searches it with the batched path
-// of rr_range_search, and splits the CSR into per-request results.  With two
-// or more workers one batch's host-side assembly overlaps the next batch's
-// kernels.  Admission is by result memory: the match counts of range queries
-// are heavy-tailed (Sec. 3), so a count of requests is no bound on memory.
+// whatever is queued when it becomes free, and searches it with the batched
+// path of rr_range_search.  The batch's CSR stays where the search left it
+// (host memory, or device memory with result_on_device) and is shared by the
+// batch's requests; a request's row is copied out once, when it is collected
+// (a gather kernel for device results).  With two or more workers one batch's
+// host-side work overlaps the next batch's kernels.  Admission is by result
+// memory: the match counts of range queries are heavy-tailed (Sec. 3), so a
+// count of requests is no bound on memory.
 #include <stdlib.h>
 #include <string.h>
 
@@ -15,6 +18,7 @@
 #include <chrono>
 #include <condition_variable>
 #include <deque>
+#include <memory>
 #include <mutex>
 #include <new>
 #include <thread>
@@ -35,11 +39,30 @@ struct Request {
     Clock::time_point t0;
 };
 
+// One search's result, shared by the requests of its batch until the last is collected.
+struct Batch {
+    rr_result res;                 // host or device CSR of the batch
+    std::vector<int64_t> off;      // host copy of the offsets (device results)
+    std::vector<uint8_t> flags;    // host copy of the flags (device results)
+    std::vector<rr_query_stats> stats;
+    Batch() { memset(&res, 0, sizeof res); }
+    ~Batch() { rr_result_free(&res); }
+    int64_t lo(int64_t i) const { return res.on_device ? off[i] : res.offsets[i]; }
+    int64_t count(int64_t i) const { return lo(i + 1) - lo(i); }
+    uint8_t flag(int64_t i) const { return res.on_device ? flags[i] : res.flags[i]; }
+    rr_query_stats stat(int64_t i) const {
+        if (res.on_device) return stats.empty() ? rr_query_stats{} : stats[i];
+        return res.stats ? res.stats[i] : rr_query_stats{};
+    }
+};
+
 struct Done {
-    rr_status status;
+    rr_status status = RR_OK;
     std::string err;
-    rr_result res;  // nq = 1, host arrays
-    int64_t bytes;  // held against the budget until polled
+    std::shared_ptr<Batch> batch;  // null for a failed or canceled request
+    int64_t idx = 0;               // the request's row in the batch
+    int64_t bytes = 0;             // held against the budget until collected
+    uint8_t flag = 0;
 };
 
 struct Worker {
@@ -49,6 +72,26 @@ struct Worker {
     uint8_t *qpin = nullptr;  // pinned batch of queries
     size_t qpin_cap = 0;
 };
+
+// segment copy for device results: row i of the output comes from src[i]
+struct Seg {
+    const uint32_t *ids;
+    const uint32_t *dists;
+    int64_t len;
+    int64_t dst;
+};
+
+__global__ void gather_segments_kernel(const Seg *segs, int64_t n, uint32_t *ids, uint32_t *dists) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t s = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); s < n; s += nw) {
+        const Seg g = segs[s];
+        for (int64_t k = lane; k < g.len; k += 32) {
+            ids[g.dst + k] = g.ids[k];
+            dists[g.dst + k] = g.dists[k];
+        }
+    }
+}
 
 }  // namespace
 
@@ -64,16 +107,23 @@ struct rr_server {
     std::vector<uint8_t> qbuf;
     size_t qbuf_head = 0;
     std::unordered_map<uint64_t, Done> done;
-    std::unordered_map<uint64_t, int> live;  // queued or in flight or done-not-polled
+    std::unordered_map<uint64_t, int> live;  // queued or in flight or done-not-collected
     uint64_t next_ticket = 1;
     int64_t bytes_held = 0;
     int64_t in_flight = 0;
+    double reserve = 0;       // bytes reserved per admitted request (fixed, or a running mean)
+    bool adaptive = false;
     bool stop = false;
     // statistics since the last reset
-    int64_t submitted = 0, completed = 0, polled = 0, batches = 0, batched = 0, admission_waits = 0;
+    int64_t submitted = 0, completed = 0, polled = 0, batches = 0, batched = 0, admission_waits = 0, canceled = 0;
     std::vector<float> lat_us;
     Clock::time_point t_reset;
     std::vector<Worker> workers;
+    // collection of device results (one collector at a time)
+    std::mutex cmu;
+    cudaStream_t cst = nullptr;
+    uint8_t *cpin = nullptr;
+    size_t cpin_cap = 0;
 };
 
 namespace {
@@ -82,37 +132,11 @@ int64_t result_bytes(int64_t count, bool stats) {
     return 8 * count + 16 + 1 + (stats ? (int64_t)sizeof(rr_query_stats) : 0);
 }
 
-// Split a host CSR result into single-query results (one per request).
-rr_status split_one(const rr_result &b, int64_t i, bool stats, rr_result *o) {
-    memset(o, 0, sizeof *o);
-    const int64_t lo = b.offsets[i], cnt = b.offsets[i + 1] - lo;
-    o->nq = 1;
-    o->total = cnt;
-    o->dist_dtype = b.dist_dtype;
-    o->offsets = (int64_t *)malloc(2 * sizeof(int64_t));
-    o->ids = (uint32_t *)malloc((size_t)std::max<int64_t>(cnt, 1) * 4);
-    o->dists = malloc((size_t)std::max<int64_t>(cnt, 1) * 4);
-    o->flags = (uint8_t *)malloc(1);
-    if (stats) o->stats = (rr_query_stats *)malloc(sizeof(rr_query_stats));
-    if (!o->offsets || !o->ids || !o->dists || !o->flags || (stats && !o->stats)) {
-        rr_result_free(o);
-        return RR_ENOMEM;
-    }
-    o->offsets[0] = 0;
-    o->offsets[1] = cnt;
-    if (cnt) {
-        memcpy(o->ids, b.ids + lo, (size_t)cnt * 4);
-        memcpy(o->dists, (const uint8_t *)b.dists + lo * 4, (size_t)cnt * 4);
-    }
-    o->flags[0] = b.flags[i];
-    if (stats) o->stats[0] = b.stats ? b.stats[i] : rr_query_stats{};
-    return RR_OK;
-}
-
 void worker_loop(rr_server *S, Worker *W) {
     DeviceGuard dg(S->ix->device);
     const rr_serve_cfg &C = S->cfg;
     const bool stats = C.params.collect_stats != 0;
+    const bool dev = C.result_on_device != 0;
     std::vector<Request> batch;
     std::vector<double> radii;
     for (;;) {
@@ -126,20 +150,21 @@ void worker_loop(rr_server *S, Worker *W) {
                 S->cv_work.wait_until(lk, until, [&] { return S->stop || (int64_t)S->queue.size() >= C.max_batch; });
                 if (S->queue.empty()) continue;  // another worker took them
             }
-            // admission: each request reserves reserve_per_request bytes of the budget
+            // admission: each request reserves S->reserve bytes of the budget
+            const int64_t per = (int64_t)S->reserve;
             batch.clear();
             while (!S->queue.empty() && (int64_t)batch.size() < C.max_batch) {
-                bool fits = S->bytes_held + reserved + C.reserve_per_request <= C.result_budget_bytes;
+                bool fits = S->bytes_held + reserved + per <= C.result_budget_bytes;
                 // always admit one when nothing is held; a stopping server drains its queue regardless
                 bool progress = S->bytes_held + reserved == 0 || S->stop;
                 if (!fits && !progress) break;
                 batch.push_back(S->queue.front());
                 S->queue.pop_front();
-                reserved += C.reserve_per_request;
+                reserved += per;
             }
             if (batch.empty()) {
                 S->admission_waits++;
-                // wait for a poll to free budget (or stop); re-check from the top
+                // wait for a collection to free budget (or stop); re-check from the top
                 S->cv_work.wait_for(lk, std::chrono::milliseconds(50));
                 continue;
             }
@@ -172,35 +197,56 @@ void worker_loop(rr_server *S, Worker *W) {
         int64_t cap = std::max<int64_t>(budget_left, reserved) / 8;
         if (P.max_results_total > 0) cap = std::min<int64_t>(cap, P.max_results_total);
         P.max_results_total = std::max<int64_t>(cap, 1);
-        rr_result res;
-        memset(&res, 0, sizeof res);
-        rr_status s = W->qpin ? rr_range_search(W->view, W->qpin, k, radii.data(), 0.0, C.variant, &P, W->st, 0, &res)
+        auto B = std::make_shared<Batch>();
+        rr_status s = W->qpin ? rr_range_search(W->view, W->qpin, k, radii.data(), 0.0, C.variant, &P, W->st,
+                                                dev ? 1 : 0, &B->res)
                               : RR_ENOMEM;
         if (s == RR_EOVERFLOW) s = RR_OK;  // truncated results are flagged per query
+        if (s == RR_OK && dev) {
+            // row bounds, flags (and counters) of the device CSR, for collection and accounting
+            B->off.resize((size_t)k + 1);
+            B->flags.resize((size_t)k);
+            cudaError_t e = cudaMemcpyAsync(B->off.data(), B->res.offsets, (size_t)(k + 1) * 8, cudaMemcpyDeviceToHost, W->st);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(B->flags.data(), B->res.flags, (size_t)k, cudaMemcpyDeviceToHost, W->st);
+            if (e == cudaSuccess && stats && B->res.stats) {
+                B->stats.resize((size_t)k);
+                e = cudaMemcpyAsync(B->stats.data(), B->res.stats, (size_t)k * sizeof(rr_query_stats),
+                                    cudaMemcpyDeviceToHost, W->st);
+            }
+            if (e == cudaSuccess) e = cudaStreamSynchronize(W->st);
+            if (e != cudaSuccess) s = cuda_fail(e, "rr_serve: reading a batch's row bounds");
+        }
         std::string err = s == RR_OK ? std::string() : std::string(rr_last_error());
-        std::vector<Done> out(k);
+        std::vector<Done> out((size_t)k);
+        int64_t batch_bytes = 0;
         for (int64_t j = 0; j < k; j++) {
-            memset(&out[j].res, 0, sizeof out[j].res);
-            out[j].status = s;
-            out[j].err = err;
-            out[j].bytes = 0;
+            Done &d = out[(size_t)j];
+            d.status = s;
+            d.err = err;
             if (s == RR_OK) {
-                rr_status t = split_one(res, j, stats, &out[j].res);
-                if (t != RR_OK) { out[j].status = t; out[j].err = "result allocation failed"; }
-                else out[j].bytes = result_bytes(out[j].res.total, stats);
+                d.batch = B;
+                d.idx = j;
+                d.flag = B->flag(j);
+                d.bytes = result_bytes(B->count(j), stats);
+                batch_bytes += d.bytes;
             }
         }
-        rr_result_free(&res);
+        B.reset();
         const Clock::time_point t1 = Clock::now();
         {
             std::lock_guard<std::mutex> lk(S->mu);
             S->bytes_held -= reserved;
             S->in_flight -= k;
             for (int64_t j = 0; j < k; j++) {
-                S->bytes_held += out[j].bytes;
-                S->lat_us.push_back(
-                    (float)std::chrono::duration<double, std::micro>(t1 - batch[j].t0).count());
-                S->done.emplace(batch[j].ticket, std::move(out[j]));
+                S->bytes_held += out[(size_t)j].bytes;
+                S->lat_us.push_back((float)std::chrono::duration<double, std::micro>(t1 - batch[j].t0).count());
+                S->done.emplace(batch[j].ticket, std::move(out[(size_t)j]));
+            }
+            if (S->adaptive && s == RR_OK && k > 0) {
+                // running mean of the bytes a request turns out to hold (never below the beam's share)
+                const double floor_b = 8.0 * C.params.beam + 32.0;
+                S->reserve = std::max(floor_b, 0.8 * S->reserve + 0.2 * ((double)batch_bytes / (double)k));
             }
             S->completed += k;
             S->batches += 1;
@@ -209,6 +255,170 @@ void worker_loop(rr_server *S, Worker *W) {
         S->cv_done.notify_all();
         S->cv_work.notify_all();  // budget may have shrunk or grown
     }
+}
+
+// Take tickets first .. first+n-1 out of the done table (all must be done); caller holds S->mu.
+void take_done(rr_server *S, uint64_t first, int64_t n, std::vector<Done> &got) {
+    got.resize((size_t)n);
+    int64_t freed = 0;
+    for (int64_t i = 0; i < n; i++) {
+        auto it = S->done.find(first + (uint64_t)i);
+        got[(size_t)i] = std::move(it->second);
+        S->done.erase(it);
+        S->live.erase(first + (uint64_t)i);
+        freed += got[(size_t)i].bytes;
+    }
+    S->bytes_held -= freed;
+    S->polled += n;
+}
+
+// Build one CSR (host or device) from collected requests.
+rr_status assemble(rr_server *S, std::vector<Done> &got, rr_result *out) {
+    const int64_t n = (int64_t)got.size();
+    const bool stats = S->cfg.params.collect_stats != 0;
+    const bool dev = S->cfg.result_on_device != 0;
+    std::vector<int64_t> off((size_t)n + 1);
+    std::vector<uint8_t> fl((size_t)n);
+    std::vector<rr_query_stats> st(stats ? (size_t)n : 0);
+    int64_t total = 0;
+    for (int64_t i = 0; i < n; i++) {
+        const Done &d = got[(size_t)i];
+        off[(size_t)i] = total;
+        fl[(size_t)i] = d.flag;
+        if (d.batch) {
+            total += d.batch->count(d.idx);
+            if (stats) st[(size_t)i] = d.batch->stat(d.idx);
+        }
+    }
+    off[(size_t)n] = total;
+    memset(out, 0, sizeof *out);
+    out->nq = n;
+    out->total = total;
+    out->dist_dtype = S->ix->dtype == RR_F32 ? 1 : 0;
+    if (!dev) {
+        out->offsets = (int64_t *)malloc((size_t)(n + 1) * 8);
+        out->ids = (uint32_t *)malloc((size_t)std::max<int64_t>(total, 1) * 4);
+        out->dists = malloc((size_t)std::max<int64_t>(total, 1) * 4);
+        out->flags = (uint8_t *)malloc((size_t)std::max<int64_t>(n, 1));
+        if (stats) out->stats = (rr_query_stats *)malloc((size_t)std::max<int64_t>(n, 1) * sizeof(rr_query_stats));
+        if (!out->offsets || !out->ids || !out->dists || !out->flags || (stats && !out->stats)) {
+            rr_result_free(out);
+            set_error("rr_serve: result allocation failed");
+            return RR_ENOMEM;
+        }
+        memcpy(out->offsets, off.data(), (size_t)(n + 1) * 8);
+        if (n) memcpy(out->flags, fl.data(), (size_t)n);
+        if (stats && n) memcpy(out->stats, st.data(), (size_t)n * sizeof(rr_query_stats));
+        for (int64_t i = 0; i < n; i++) {
+            const Done &d = got[(size_t)i];
+            const int64_t c = d.batch ? d.batch->count(d.idx) : 0;
+            if (!c) continue;
+            const int64_t lo = d.batch->lo(d.idx);
+            memcpy(out->ids + off[(size_t)i], d.batch->res.ids + lo, (size_t)c * 4);
+            memcpy((uint8_t *)out->dists + off[(size_t)i] * 4, (const uint8_t *)d.batch->res.dists + lo * 4, (size_t)c * 4);
+        }
+        return RR_OK;
+    }
+    // device results: one gather launch on the server's collection stream
+    std::lock_guard<std::mutex> ck(S->cmu);
+    DeviceGuard dg(S->ix->device);
+    cudaStream_t cs = S->cst;
+    int64_t nseg = 0;
+    for (auto &d : got) nseg += d.batch && d.batch->count(d.idx) > 0;
+    const size_t seg_bytes = (size_t)nseg * sizeof(Seg);
+    const size_t head = (size_t)(n + 1) * 8 + (size_t)n + (stats ? (size_t)n * sizeof(rr_query_stats) : 0);
+    const size_t pin_need = ((head + 15) & ~(size_t)15) + seg_bytes;
+    if (pin_need > S->cpin_cap) {
+        if (S->cpin) { cudaStreamSynchronize(cs); cudaFreeHost(S->cpin); }
+        S->cpin = nullptr;
+        S->cpin_cap = 0;
+        if (cudaMallocHost(&S->cpin, std::max(pin_need, (size_t)1 << 20)) != cudaSuccess) {
+            cudaGetLastError();
+            set_error("rr_serve: pinned staging allocation failed");
+            return RR_ENOMEM;
+        }
+        S->cpin_cap = std::max(pin_need, (size_t)1 << 20);
+    }
+    RR_CUDA(cudaStreamSynchronize(cs));  // the staging may still feed the previous collection's copies
+    uint8_t *hp = S->cpin;
+    memcpy(hp, off.data(), (size_t)(n + 1) * 8);
+    if (n) memcpy(hp + (size_t)(n + 1) * 8, fl.data(), (size_t)n);
+    if (stats && n) memcpy(hp + (size_t)(n + 1) * 8 + (size_t)n, st.data(), (size_t)n * sizeof(rr_query_stats));
+    Seg *hs = reinterpret_cast<Seg *>(hp + ((head + 15) & ~(size_t)15));
+    int64_t k = 0;
+    for (int64_t i = 0; i < n; i++) {
+        const Done &d = got[(size_t)i];
+        const int64_t c = d.batch ? d.batch->count(d.idx) : 0;
+        if (!c) continue;
+        const int64_t lo = d.batch->lo(d.idx);
+        hs[k++] = Seg{d.batch->res.ids + lo, (const uint32_t *)d.batch->res.dists + lo, c, off[(size_t)i]};
+    }
+    out->on_device = 1;
+    out->_stream = (void *)cs;
+    out->_device = S->ix->device;
+    Seg *dsegs = nullptr;
+    cudaError_t e = cudaMallocAsync((void **)&out->offsets, (size_t)(n + 1) * 8, cs);
+    if (e == cudaSuccess) e = cudaMallocAsync((void **)&out->ids, (size_t)std::max<int64_t>(total, 1) * 4, cs);
+    if (e == cudaSuccess) e = cudaMallocAsync(&out->dists, (size_t)std::max<int64_t>(total, 1) * 4, cs);
+    if (e == cudaSuccess) e = cudaMallocAsync((void **)&out->flags, (size_t)std::max<int64_t>(n, 1), cs);
+    if (e == cudaSuccess && stats)
+        e = cudaMallocAsync((void **)&out->stats, (size_t)std::max<int64_t>(n, 1) * sizeof(rr_query_stats), cs);
+    if (e == cudaSuccess && nseg) e = cudaMallocAsync((void **)&dsegs, seg_bytes, cs);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out->offsets, hp, (size_t)(n + 1) * 8, cudaMemcpyHostToDevice, cs);
+    if (e == cudaSuccess && n) e = cudaMemcpyAsync(out->flags, hp + (size_t)(n + 1) * 8, (size_t)n, cudaMemcpyHostToDevice, cs);
+    if (e == cudaSuccess && stats && n)
+        e = cudaMemcpyAsync(out->stats, hp + (size_t)(n + 1) * 8 + (size_t)n, (size_t)n * sizeof(rr_query_stats),
+                            cudaMemcpyHostToDevice, cs);
+    if (e == cudaSuccess && nseg) e = cudaMemcpyAsync(dsegs, hs, seg_bytes, cudaMemcpyHostToDevice, cs);
+    if (e == cudaSuccess && nseg) {
+        const int blocks = (int)std::min<int64_t>((nseg + 7) / 8, 152 * 16);
+        gather_segments_kernel<<<blocks, 256, 0, cs>>>(dsegs, nseg, out->ids, (uint32_t *)out->dists);
+        note_launch();
+        e = cudaGetLastError();
+    }
+    if (dsegs) cudaFreeAsync(dsegs, cs);
+    // the batches' arrays are released when the caller drops them: finish reading them first
+    if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
+    if (e != cudaSuccess) {
+        rr_result_free(out);
+        return cuda_fail(e, "rr_serve: gathering device results");
+    }
+    return RR_OK;
+}
+
+rr_status collect_impl(rr_server *S, uint64_t first, int64_t n, int32_t timeout_ms, rr_result *out, const char *who) {
+    std::vector<Done> got;
+    {
+        std::unique_lock<std::mutex> lk(S->mu);
+        for (int64_t i = 0; i < n; i++)
+            if (!S->live.count(first + (uint64_t)i)) {
+                set_error("%s: unknown or retired ticket %llu", who, (unsigned long long)(first + i));
+                return RR_EINVAL;
+            }
+        auto ready = [&] {
+            for (int64_t i = 0; i < n; i++)
+                if (!S->done.count(first + (uint64_t)i)) return false;
+            return true;
+        };
+        if (!ready()) {
+            if (timeout_ms <= 0) return RR_EBUSY;
+            if (!S->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), ready)) return RR_EBUSY;
+        }
+        take_done(S, first, n, got);
+    }
+    S->cv_work.notify_all();
+    rr_status bad = RR_OK;
+    std::string err;
+    for (auto &g : got)
+        if (g.status != RR_OK && bad == RR_OK) { bad = g.status; err = g.err; }
+    rr_status s = assemble(S, got, out);
+    got.clear();  // drops the batch references (after any gather has finished reading them)
+    if (s != RR_OK) return s;
+    if (bad != RR_OK) {  // the requests are retired either way; report the first failure
+        set_error("%s", err.c_str());
+        return bad;
+    }
+    return RR_OK;
 }
 
 }  // namespace
@@ -224,7 +434,8 @@ void rr_serve_cfg_init(rr_serve_cfg *c) {
     c->variant = RR_GREEDY_ES;
     rr_params_init(&c->params);
     c->result_budget_bytes = (int64_t)4 << 30;
-    c->reserve_per_request = 0;  // 0: 8 bytes per beam slot
+    c->reserve_per_request = 0;  // 0: a running mean of the bytes requests hold
+    c->result_on_device = 0;
 }
 
 rr_status rr_serve_create(rr_index *ix, const rr_serve_cfg *cfg, rr_server **out) {
@@ -233,11 +444,11 @@ rr_status rr_serve_create(rr_index *ix, const rr_serve_cfg *cfg, rr_server **out
     rr_serve_cfg C;
     if (cfg) C = *cfg; else rr_serve_cfg_init(&C);
     if (C.workers < 1 || C.workers > 64 || C.max_batch < 1 || C.batch_wait_us < 0 || C.result_budget_bytes <= 0 ||
-        C.reserve_per_request < 0 || C.variant < RR_BEAM || C.variant > RR_GREEDY_ES || C.params.beam < 1) {
+        C.reserve_per_request < 0 || C.variant < RR_BEAM || C.variant > RR_GREEDY_ES || C.params.beam < 1 ||
+        (C.result_on_device != 0 && C.result_on_device != 1)) {
         set_error("rr_serve_create: invalid configuration");
         return RR_EINVAL;
     }
-    if (C.reserve_per_request == 0) C.reserve_per_request = 8 * (int64_t)C.params.beam + 32;
     if (C.params.precision != RR_PREC_EXACT && ix->dtype != RR_F32) {
         set_error("rr_serve_create: the precision form needs an fp32 index");
         return RR_EINVAL;
@@ -253,22 +464,26 @@ rr_status rr_serve_create(rr_index *ix, const rr_serve_cfg *cfg, rr_server **out
     if (!S) { set_error("rr_serve_create: out of memory"); return RR_ENOMEM; }
     S->ix = ix;
     S->cfg = C;
+    S->adaptive = C.reserve_per_request == 0;
+    S->reserve = S->adaptive ? 8.0 * C.params.beam + 32.0 : (double)C.reserve_per_request;
     S->row_bytes = (size_t)ix->d * elem_size(ix->dtype);
     S->t_reset = Clock::now();
     S->workers.resize(C.workers);
+    bool ok = cudaStreamCreateWithFlags(&S->cst, cudaStreamNonBlocking) == cudaSuccess;
     for (auto &W : S->workers) {
         W.view = index_worker_view(ix);
-        cudaError_t e = cudaStreamCreateWithFlags(&W.st, cudaStreamNonBlocking);
-        if (!W.view || e != cudaSuccess) {
-            cudaGetLastError();
-            for (auto &V : S->workers) {
-                if (V.view) rr_free_index(V.view);
-                if (V.st) cudaStreamDestroy(V.st);
-            }
-            delete S;
-            set_error("rr_serve_create: worker set-up failed");
-            return RR_ENOMEM;
+        ok = ok && W.view && cudaStreamCreateWithFlags(&W.st, cudaStreamNonBlocking) == cudaSuccess;
+    }
+    if (!ok) {
+        cudaGetLastError();
+        for (auto &V : S->workers) {
+            if (V.view) rr_free_index(V.view);
+            if (V.st) cudaStreamDestroy(V.st);
         }
+        if (S->cst) cudaStreamDestroy(S->cst);
+        delete S;
+        set_error("rr_serve_create: worker set-up failed");
+        return RR_ENOMEM;
     }
     for (auto &W : S->workers) W.th = std::thread(worker_loop, S, &W);
     *out = S;
@@ -317,101 +532,33 @@ rr_status rr_serve_submit(rr_server *S, const void *queries, int64_t n, const do
 rr_status rr_serve_poll(rr_server *S, uint64_t ticket, int32_t timeout_ms, rr_result *out) {
     if (!S || !out) { set_error("rr_serve_poll: NULL argument"); return RR_EINVAL; }
     memset(out, 0, sizeof *out);
-    std::unique_lock<std::mutex> lk(S->mu);
-    if (!S->live.count(ticket)) { set_error("rr_serve_poll: unknown or retired ticket %llu", (unsigned long long)ticket); return RR_EINVAL; }
-    auto ready = [&] { return S->done.count(ticket) != 0; };
-    if (!ready()) {
-        if (timeout_ms <= 0) return RR_EBUSY;
-        if (!S->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), ready)) return RR_EBUSY;
-    }
-    auto it = S->done.find(ticket);
-    Done d = std::move(it->second);
-    S->done.erase(it);
-    S->live.erase(ticket);
-    S->bytes_held -= d.bytes;
-    S->polled++;
-    lk.unlock();
-    S->cv_work.notify_all();
-    if (d.status != RR_OK) {
-        set_error("%s", d.err.c_str());
-        return d.status;
-    }
-    *out = d.res;
-    return RR_OK;
+    return collect_impl(S, ticket, 1, timeout_ms, out, "rr_serve_poll");
 }
 
 rr_status rr_serve_collect(rr_server *S, uint64_t first, int64_t n, int32_t timeout_ms, rr_result *out) {
     if (!S || !out || n < 0) { set_error("rr_serve_collect: bad argument"); return RR_EINVAL; }
     memset(out, 0, sizeof *out);
-    std::unique_lock<std::mutex> lk(S->mu);
-    for (int64_t i = 0; i < n; i++)
-        if (!S->live.count(first + (uint64_t)i)) {
-            set_error("rr_serve_collect: unknown or retired ticket %llu", (unsigned long long)(first + i));
-            return RR_EINVAL;
+    return collect_impl(S, first, n, timeout_ms, out, "rr_serve_collect");
+}
+
+int64_t rr_serve_cancel(rr_server *S) {
+    if (!S) return 0;
+    int64_t k = 0;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        while (!S->queue.empty()) {
+            Done d;
+            d.flag = RR_FLAG_CANCELED;
+            S->done.emplace(S->queue.front().ticket, std::move(d));
+            S->queue.pop_front();
+            k++;
         }
-    auto ready = [&] {
-        for (int64_t i = 0; i < n; i++)
-            if (!S->done.count(first + (uint64_t)i)) return false;
-        return true;
-    };
-    if (!ready()) {
-        if (timeout_ms <= 0) return RR_EBUSY;
-        if (!S->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), ready)) return RR_EBUSY;
+        S->qbuf.clear();
+        S->qbuf_head = 0;
+        S->canceled += k;
     }
-    std::vector<Done> got((size_t)n);
-    int64_t total = 0, freed = 0;
-    for (int64_t i = 0; i < n; i++) {
-        auto it = S->done.find(first + (uint64_t)i);
-        got[(size_t)i] = std::move(it->second);
-        S->done.erase(it);
-        S->live.erase(first + (uint64_t)i);
-        freed += got[(size_t)i].bytes;
-        total += got[(size_t)i].status == RR_OK ? got[(size_t)i].res.total : 0;
-    }
-    S->bytes_held -= freed;
-    S->polled += n;
-    lk.unlock();
-    S->cv_work.notify_all();
-    rr_status bad = RR_OK;
-    std::string err;
-    for (auto &g : got)
-        if (g.status != RR_OK && bad == RR_OK) { bad = g.status; err = g.err; }
-    const bool stats = S->cfg.params.collect_stats != 0;
-    out->nq = n;
-    out->total = total;
-    out->dist_dtype = S->ix->dtype == RR_F32 ? 1 : 0;
-    out->offsets = (int64_t *)malloc((size_t)(n + 1) * 8);
-    out->ids = (uint32_t *)malloc((size_t)std::max<int64_t>(total, 1) * 4);
-    out->dists = malloc((size_t)std::max<int64_t>(total, 1) * 4);
-    out->flags = (uint8_t *)malloc((size_t)std::max<int64_t>(n, 1));
-    if (stats) out->stats = (rr_query_stats *)calloc((size_t)std::max<int64_t>(n, 1), sizeof(rr_query_stats));
-    const bool ok = out->offsets && out->ids && out->dists && out->flags && (!stats || out->stats);
-    int64_t pos = 0;
-    for (int64_t i = 0; i < n; i++) {
-        rr_result &r = got[(size_t)i].res;
-        if (ok) {
-            out->offsets[i] = pos;
-            out->flags[i] = got[(size_t)i].status == RR_OK ? r.flags[0] : 0;
-            if (got[(size_t)i].status == RR_OK && r.total) {
-                memcpy(out->ids + pos, r.ids, (size_t)r.total * 4);
-                memcpy((uint8_t *)out->dists + pos * 4, r.dists, (size_t)r.total * 4);
-                pos += r.total;
-            }
-            if (stats && r.stats) out->stats[i] = r.stats[0];
-        }
-        rr_result_free(&r);
-    }
-    if (!ok) {
-        rr_result_free(out);
-        set_error("rr_serve_collect: result allocation failed");
-        return RR_ENOMEM;
-    }
-    out->offsets[n] = pos;
-    if (bad != RR_OK) {  // the requests are retired either way; report the first failure
-        set_error("%s", err.c_str());
-        return bad;
-    }
-    return RR_OK;
+    S->cv_done.notify_all();
+    return k;
 }
 
 rr_status rr_serve_stats(rr_server *S, rr_serve_stats_t *o, int32_t reset) {
@@ -427,6 +574,8 @@ rr_status rr_serve_stats(rr_server *S, rr_serve_stats_t *o, int32_t reset) {
     o->mean_batch = S->batches ? (double)S->batched / S->batches : 0.0;
     o->bytes_held = S->bytes_held;
     o->admission_waits = S->admission_waits;
+    o->canceled = S->canceled;
+    o->reserve_per_request = (int64_t)S->reserve;
     const double secs = std::chrono::duration<double>(Clock::now() - S->t_reset).count();
     o->qps = secs > 0 ? S->completed / secs : 0.0;
     if (!S->lat_us.empty()) {
@@ -444,7 +593,7 @@ rr_status rr_serve_stats(rr_server *S, rr_serve_stats_t *o, int32_t reset) {
         o->max_us = mx;
     }
     if (reset) {
-        S->submitted = S->completed = S->polled = S->batches = S->batched = S->admission_waits = 0;
+        S->submitted = S->completed = S->polled = S->batches = S->batched = S->admission_waits = S->canceled = 0;
         S->lat_us.clear();
         S->t_reset = Clock::now();
     }
@@ -461,13 +610,18 @@ rr_status rr_serve_destroy(rr_server *S) {
     for (auto &W : S->workers)
         if (W.th.joinable()) W.th.join();
     DeviceGuard dg(S->ix->device);
+    S->done.clear();  // releases the batches nobody collected
     for (auto &W : S->workers) {
         if (W.st) cudaStreamSynchronize(W.st);
         if (W.view) rr_free_index(W.view);
         if (W.st) cudaStreamDestroy(W.st);
         if (W.qpin) cudaFreeHost(W.qpin);
     }
-    for (auto &kv : S->done) rr_result_free(&kv.second.res);
+    if (S->cst) {
+        cudaStreamSynchronize(S->cst);
+        cudaStreamDestroy(S->cst);
+    }
+    if (S->cpin) cudaFreeHost(S->cpin);
     delete S;
     return RR_OK;
 }

@@ -150,3 +150,38 @@ def test_collect_returns_a_submission_as_one_csr(env):
                 ids, d = res.query(j)
                 assert np.array_equal(ids, o_ids[s + j]) and np.array_equal(d.astype(np.int64), o_d[s + j])
         assert srv.stats()["bytes_held"] == 0
+
+
+def test_device_results_equal_the_oracle(env):
+    rr, ds, gi, radii, o_ids, o_d = env
+    with gi.serve(workers=3, max_batch=97, batch_wait_us=50, beam=32, result_on_device=1) as srv:
+        firsts = [(s, srv.submit(ds.Q[s:s + 100], radii[s:s + 100])[0]) for s in range(0, 1000, 100)]
+        for s, t0 in firsts[::2]:
+            res = srv.collect(t0, 100, timeout_ms=60_000)  # gathered on the device, copied here for checking
+            for j in range(100):
+                ids, d = res.query(j)
+                assert np.array_equal(ids, o_ids[s + j]) and np.array_equal(d.astype(np.int64), o_d[s + j])
+        for s, t0 in firsts[1::2]:
+            for j in range(100):
+                r = srv.poll(t0 + j, timeout_ms=60_000)
+                assert np.array_equal(r.query(0)[0], o_ids[s + j])
+        st = srv.stats()
+        assert st["bytes_held"] == 0 and st["completed"] == 1000
+
+
+def test_cancel_drops_only_queued_requests(env):
+    rr, ds, gi, radii, o_ids, o_d = env
+    with gi.serve(workers=1, max_batch=8, batch_wait_us=0, beam=32) as srv:
+        t0 = srv.submit(ds.Q, radii)[0]
+        dropped = srv.cancel()
+        res = srv.collect(t0, len(ds.Q), timeout_ms=60_000)
+        canceled = (res.flags & rr.RR_FLAG_CANCELED) != 0
+        assert int(canceled.sum()) == dropped
+        for i in range(len(ds.Q)):
+            ids, d = res.query(i)
+            if canceled[i]:
+                assert len(ids) == 0
+            else:
+                assert np.array_equal(ids, o_ids[i])
+        st = srv.stats()
+        assert st["canceled"] == dropped and st["queued"] == 0 and st["bytes_held"] == 0
