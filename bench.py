@@ -215,12 +215,13 @@ def run_serve(args, cfg, ds, rr, gi, stream, dev):
         t_arr = np.cumsum(gaps)
         pick = rs.integers(0, nq, n_arr)
         srv = gi.serve(workers=args.serve_workers, max_batch=args.serve_max_batch, batch_wait_us=args.serve_wait_us,
-                       variant=variant, result_budget_bytes=1 << 32, **base)
+                       variant=variant, result_budget_bytes=4 << 30, result_on_device=args.serve_device, **base)
         subs = []
         lock = threading.Condition()
         done = {"gen": False}
         lag = []
-        collected = [0, 0]
+        collected = [0, 0, 0]  # requests served, their results, requests canceled
+        t_last = [0.0]
 
         def collector():
             k = 0
@@ -237,6 +238,7 @@ def run_serve(args, cfg, ds, rr, gi, stream, dev):
                     if st == rr.RR_OK:
                         collected[0] += cnt
                         collected[1] += res.total
+                        t_last[0] = time.perf_counter()
                         rr.rr_result_free(res)
                         break
 
@@ -261,23 +263,32 @@ def run_serve(args, cfg, ds, rr, gi, stream, dev):
         with lock:
             done["gen"] = True
             lock.notify()
+        # the window closes serve_secs after the last arrival: what is still queued then is dropped
+        th.join(timeout=args.serve_secs)
+        dropped = rr.rr_serve_cancel(srv.h) if th.is_alive() else 0
         th.join()
-        wall = time.perf_counter() - ts
         sst = rr.rr_serve_stats(srv.h).as_dict()
+        served = sst["completed"]
+        wall = max(t_last[0] - ts, 1e-9)
         srv.close()
-        row = {"offered_frac": frac, "offered_qps": rate, "achieved_qps": collected[0] / wall,
+        row = {"offered_frac": frac, "offered_qps": rate, "achieved_qps": served / wall, "served": served,
+               "canceled": dropped, "reserve_per_request": sst["reserve_per_request"],
+               "admission_waits": sst["admission_waits"],
                "p50_us": sst["p50_us"], "p99_us": sst["p99_us"], "mean_us": sst["mean_us"], "max_us": sst["max_us"],
                "mean_batch": sst["mean_batch"], "batches": sst["batches"], "requests": collected[0],
-               "results": collected[1], "generator_lag_p99_us": float(np.percentile(lag, 99) * 1e6) if lag else 0.0}
+               "results": collected[1], "results_per_served_request": collected[1] / max(1, served), "generator_lag_p99_us": float(np.percentile(lag, 99) * 1e6) if lag else 0.0}
         rows.append(row)
-        log("serve: offered %.0f QPS (%.2f of batch) -> %.0f QPS, p50 %.0f us, p99 %.0f us, mean batch %.0f" % (
-            rate, frac, row["achieved_qps"], row["p50_us"], row["p99_us"], row["mean_batch"]))
+        log("serve: offered %.0f QPS (%.2f of batch) -> %.0f QPS, p50 %.0f us, p99 %.0f us, mean batch %.0f, "
+            "canceled %d" % (rate, frac, row["achieved_qps"], row["p50_us"], row["p99_us"], row["mean_batch"], dropped))
     line = {"metric": "serving latency under open-loop Poisson load", "unit": "us", "higher_is_better": False,
             "value": rows[-1]["p99_us"] if rows else None, "n_gpus": 1, "dtype": str(ds.X.dtype), "data": "synthetic",
             "config": {"workload": "%s: n=%d d=%d, single-query requests, radii r/1.5r/2r" % (cfg.name, cfg.n, cfg.d),
                        "variant": variant, "beam": beam, "workers": args.serve_workers,
                        "max_batch": args.serve_max_batch, "batch_wait_us": args.serve_wait_us,
-                       "seconds_per_rate": args.serve_secs, "batch_qps": batch_qps},
+                       "seconds_per_rate": args.serve_secs, "batch_qps": batch_qps,
+                       "results_in": "device memory" if args.serve_device else "host memory",
+                       "window": "arrivals for seconds_per_rate s, then as long again to drain; still queued then: "
+                                 "canceled and not counted; latency = submit to result ready"},
             "rates": rows}
     print(json.dumps(line), flush=True)
 
@@ -306,6 +317,7 @@ def main():
     ap.add_argument("--serve-workers", type=int, default=3)
     ap.add_argument("--serve-max-batch", type=int, default=4096)
     ap.add_argument("--serve-wait-us", type=int, default=100)
+    ap.add_argument("--serve-device", type=int, default=1, choices=[0, 1], help="serving results in device memory")
     args = ap.parse_args()
 
     ws, rank, local = dist_env()
