@@ -240,8 +240,8 @@ rr_status rr_beam_search_noalloc(rr_index *index, const void *queries, int64_t n
  * admitted into the next free worker and their work overlaps on the device.
  * A batch's CSR stays in host memory, or in device memory when
  * result_on_device = 1, until its requests are collected; each request's row
- * is copied out once, by rr_serve_poll / rr_serve_collect (a gather kernel for
- * device results).
+ * is copied out once, by rr_serve_poll / rr_serve_collect (device results: by
+ * the copy engines, on a stream of the highest priority).
  * Admission is by result memory, because match counts are heavy-tailed: a
  * request is admitted only while the bytes of results held (finished but not
  * yet collected, plus a reservation for each request in flight) stay within

@@ -7,7 +7,8 @@
 // path of rr_range_search.  The batch's CSR stays where the search left it
 // (host memory, or device memory with result_on_device) and is shared by the
 // batch's requests; a request's row is copied out once, when it is collected
-// (a gather kernel for device results).  With two or more workers one batch's
+// (for device results: consecutive rows of a batch as one copy-engine transfer,
+// or one gather kernel when the rows are scattered).  With two or more workers one batch's
 // host-side work overlaps the next batch's kernels.  Admission is by result
 // memory: the match counts of range queries are heavy-tailed (Sec. 3), so a
 // count of requests is no bound on memory.
@@ -345,14 +346,26 @@ rr_status assemble(rr_server *S, std::vector<Done> &got, rr_result *out) {
     if (n) memcpy(hp + (size_t)(n + 1) * 8, fl.data(), (size_t)n);
     if (stats && n) memcpy(hp + (size_t)(n + 1) * 8 + (size_t)n, st.data(), (size_t)n * sizeof(rr_query_stats));
     Seg *hs = reinterpret_cast<Seg *>(hp + ((head + 15) & ~(size_t)15));
+    // consecutive requests of one batch are consecutive rows of its CSR: one run each
     int64_t k = 0;
+    const Batch *prev_b = nullptr;
+    int64_t prev_idx = -2;
     for (int64_t i = 0; i < n; i++) {
         const Done &d = got[(size_t)i];
         const int64_t c = d.batch ? d.batch->count(d.idx) : 0;
         if (!c) continue;
         const int64_t lo = d.batch->lo(d.idx);
-        hs[k++] = Seg{d.batch->res.ids + lo, (const uint32_t *)d.batch->res.dists + lo, c, off[(size_t)i]};
+        if (k > 0 && d.batch.get() == prev_b && d.idx == prev_idx + 1 && hs[k - 1].dst + hs[k - 1].len == off[(size_t)i]) {
+            hs[k - 1].len += c;
+        } else {
+            hs[k++] = Seg{d.batch->res.ids + lo, (const uint32_t *)d.batch->res.dists + lo, c, off[(size_t)i]};
+        }
+        prev_b = d.batch.get();
+        prev_idx = d.idx;
     }
+    nseg = k;
+    // a few long runs go to the copy engines; many short ones to one gather launch
+    const bool by_copy = nseg <= 8;
     out->on_device = 1;
     out->_stream = (void *)cs;
     out->_device = S->ix->device;
@@ -363,14 +376,21 @@ rr_status assemble(rr_server *S, std::vector<Done> &got, rr_result *out) {
     if (e == cudaSuccess) e = cudaMallocAsync((void **)&out->flags, (size_t)std::max<int64_t>(n, 1), cs);
     if (e == cudaSuccess && stats)
         e = cudaMallocAsync((void **)&out->stats, (size_t)std::max<int64_t>(n, 1) * sizeof(rr_query_stats), cs);
-    if (e == cudaSuccess && nseg) e = cudaMallocAsync((void **)&dsegs, seg_bytes, cs);
+    if (e == cudaSuccess && nseg && !by_copy) e = cudaMallocAsync((void **)&dsegs, seg_bytes, cs);
     if (e == cudaSuccess) e = cudaMemcpyAsync(out->offsets, hp, (size_t)(n + 1) * 8, cudaMemcpyHostToDevice, cs);
     if (e == cudaSuccess && n) e = cudaMemcpyAsync(out->flags, hp + (size_t)(n + 1) * 8, (size_t)n, cudaMemcpyHostToDevice, cs);
     if (e == cudaSuccess && stats && n)
         e = cudaMemcpyAsync(out->stats, hp + (size_t)(n + 1) * 8 + (size_t)n, (size_t)n * sizeof(rr_query_stats),
                             cudaMemcpyHostToDevice, cs);
-    if (e == cudaSuccess && nseg) e = cudaMemcpyAsync(dsegs, hs, seg_bytes, cudaMemcpyHostToDevice, cs);
-    if (e == cudaSuccess && nseg) {
+    for (int64_t j = 0; by_copy && e == cudaSuccess && j < nseg; j++) {
+        e = cudaMemcpyAsync(out->ids + hs[j].dst, hs[j].ids, (size_t)hs[j].len * 4, cudaMemcpyDeviceToDevice, cs);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync((uint32_t *)out->dists + hs[j].dst, hs[j].dists, (size_t)hs[j].len * 4,
+                                cudaMemcpyDeviceToDevice, cs);
+    }
+    if (e == cudaSuccess && nseg && !by_copy)
+        e = cudaMemcpyAsync(dsegs, hs, (size_t)nseg * sizeof(Seg), cudaMemcpyHostToDevice, cs);
+    if (e == cudaSuccess && nseg && !by_copy) {
         const int blocks = (int)std::min<int64_t>((nseg + 7) / 8, 152 * 16);
         gather_segments_kernel<<<blocks, 256, 0, cs>>>(dsegs, nseg, out->ids, (uint32_t *)out->dists);
         note_launch();
@@ -469,7 +489,11 @@ rr_status rr_serve_create(rr_index *ix, const rr_serve_cfg *cfg, rr_server **out
     S->row_bytes = (size_t)ix->d * elem_size(ix->dtype);
     S->t_reset = Clock::now();
     S->workers.resize(C.workers);
-    bool ok = cudaStreamCreateWithFlags(&S->cst, cudaStreamNonBlocking) == cudaSuccess;
+    // collection runs at the highest stream priority: its gathers are short and should not queue
+    // behind the workers' search kernels
+    int lo_prio = 0, hi_prio = 0;
+    cudaDeviceGetStreamPriorityRange(&lo_prio, &hi_prio);
+    bool ok = cudaStreamCreateWithPriority(&S->cst, cudaStreamNonBlocking, hi_prio) == cudaSuccess;
     for (auto &W : S->workers) {
         W.view = index_worker_view(ix);
         ok = ok && W.view && cudaStreamCreateWithFlags(&W.st, cudaStreamNonBlocking) == cudaSuccess;
