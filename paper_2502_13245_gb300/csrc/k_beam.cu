@@ -17,9 +17,7 @@
 // sorted, old entry i moves right by the number of new keys below it, so only
 // the suffix after the first insertion point is touched, chunk by chunk from
 // the end.  The index of the first unvisited entry (p* of Alg. 1) is carried
-// across iterations instead of rescanning B.  The adjacency row of the likely
-// next p* is loaded during the current expansion, and the vectors of its
-// unseen neighbours are prefetched into L2 before the current merge.
+// across iterations instead of rescanning B.
 #include <algorithm>
 
 #include "rr_common.cuh"
@@ -212,23 +210,6 @@ __device__ __forceinline__ void search_query(const SearchArgs &a, int hlg, int64
             int dd = 0;
             for (int c = lane; c < nc; c += 32) dd += mark_bit(cbits, cid[c]);
             distinct += dd;
-        }
-        // The likely next p*'s adjacency row has arrived by now: pull the vectors of its
-        // neighbours not yet seen towards L2, so that the next expansion's gathers hit L2
-        // instead of waiting on HBM.  A hint only: a wrong guess costs bandwidth, not results.
-        if (pre_id != kSent) {
-            const uint8_t *vb = LP ? a.lp_vec : a.vec;
-            const int rs = LP ? a.lp_stride : a.row_stride;
-#pragma unroll
-            for (int k = 0; k < 4; k++) {
-                if (32 * k >= R) break;  // warp-uniform
-                const uint32_t j = pre[k];
-                if (j < (uint32_t)a.n) {
-                    const uint32_t sl = hslot(j, hlg - 1) << 1;
-                    if (hash[sl] != j && hash[sl + 1] != j)
-                        for (int off = 0; off < rs; off += 128) prefetch_l2(vb + (size_t)j * rs + off);
-                }
-            }
         }
         // keys that can enter: below B[b-1] when B is full, and not already in B
         const uint64_t last = (nb == b) ? (B[b - 1] | 1ull) : kEmpty;

@@ -113,8 +113,6 @@ __device__ __forceinline__ T group_sum(T v, int lpv) {
 }
 
 __device__ __forceinline__ uint4 ldg16(const uint8_t *p) { return __ldg(reinterpret_cast<const uint4 *>(p)); }
-// hint: bring the 128-byte line holding p into L2 (no register result, no fault on a valid address)
-__device__ __forceinline__ void prefetch_l2(const void *p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
 
 // Fibonacci hashing of an id into a table of 2^lg slots.
 __device__ __forceinline__ uint32_t hslot(uint32_t id, int lg) { return (id * 2654435761u) >> (32 - lg); }
