@@ -190,19 +190,26 @@ def run_serve(args, cfg, ds, rr, gi, stream, dev):
     radii = ds.radius * mult
     if ds.X.dtype != np.float32:
         radii = np.floor(radii)
-    # batch throughput of this form on the same radius mix: the scale of the offered rates
-    Qd = torch.from_numpy(ds.Q).to("cuda:%d" % dev)
-    p = rr.rr_params_init(**base)
-    for _ in range(3):
-        st, res = rr.rr_range_search(gi.h, Qd, radii, variant, p, stream=stream.cuda_stream, result_on_device=True)
+    # batch throughput of this form on the same radius mix, in batches of the server's largest size and with
+    # no cap on the results: the scale of the offered rates
+    nb = min(nq, args.serve_max_batch)
+    p = rr.rr_params_init(max_results_total=1 << 30, **base)
+    for _ in range(2):
+        Qd = torch.from_numpy(ds.Q[:nb]).to("cuda:%d" % dev)
+        st, res = rr.rr_range_search(gi.h, Qd, radii[:nb], variant, p, stream=stream.cuda_stream, result_on_device=True)
         rr.rr_result_free(res)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for _ in range(5):
-        st, res = rr.rr_range_search(gi.h, Qd, radii, variant, p, stream=stream.cuda_stream, result_on_device=True)
+    done_q = 0
+    for s0 in range(0, min(nq, 4 * nb), nb):
+        Qd = torch.from_numpy(ds.Q[s0:s0 + nb]).to("cuda:%d" % dev)
+        torch.cuda.synchronize()
+        st, res = rr.rr_range_search(gi.h, Qd, radii[s0:s0 + nb], variant, p, stream=stream.cuda_stream,
+                                     result_on_device=True)
         rr.rr_result_free(res)
+        done_q += Qd.shape[0]
     torch.cuda.synchronize()
-    batch_qps = 5 * nq / (time.perf_counter() - t0)
+    batch_qps = done_q / (time.perf_counter() - t0)
     log("serve: batch throughput of %s b=%d on the radius mix: %.0f QPS" % (variant, beam, batch_qps))
     rows = []
     Qh = np.ascontiguousarray(ds.Q)
