@@ -66,12 +66,17 @@ __device__ __forceinline__ int next_unvisited(const uint64_t *B, int n, int from
 template <int DT, int CPL, int BMAX, bool COUNT>
 __device__ __forceinline__ void search_query(const SearchArgs &a, int hlg, int64_t qi, uint8_t *base);
 
+// 8-bit searches fit 64 registers with a few bytes of spill and gain from the extra resident
+// warps; the fp32 and low-precision forms keep 80 (they would spill 100-300 bytes).
+template <int DT>
+constexpr int kBeamMinBlocks = (DT == DT_U8 || DT == DT_I8) ? 4 : 3;
+
 // One warp per query.  persistent = 0: warp w of CTA c takes query c*warps + w.
 // persistent = 1: a grid sized to the resident capacity; every warp takes the
 // next query from a device counter until the batch is done, so warps freed by
 // cheap (e.g. early-stopped) queries move on to the rest of the batch.
 template <int DT, int CPL, int BMAX, bool COUNT>
-__global__ void __launch_bounds__(256, 3) beam_kernel(SearchArgs a, int hlg, int persistent, int32_t *next_q) {
+__global__ void __launch_bounds__(256, kBeamMinBlocks<DT>) beam_kernel(SearchArgs a, int hlg, int persistent, int32_t *next_q) {
     extern __shared__ __align__(16) uint8_t smem_raw[];
     const int lane = lane_id();
     const int warp = threadIdx.x >> 5;

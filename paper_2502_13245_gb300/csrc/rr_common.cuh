@@ -9,6 +9,7 @@
 // low "visited" bit marks V membership of beam entries; compares that must
 // ignore it use (key | 1).  Ids are < 2^31.
 #pragma once
+#include <type_traits>
 #include <cuda_fp16.h>
 #include <cuda_fp8.h>
 #include <cuda_runtime.h>
@@ -156,18 +157,61 @@ __device__ __forceinline__ void eval_candidates(const SearchArgs &a, const uint4
                 v[u][k] = (c < nc && ch < a.row_chunks) ? ldg16(p + (size_t)ch * 16) : make_uint4(0, 0, 0, 0);
             }
         }
+        if constexpr (std::is_integral<T>::value) {
+            // Integer sums do not depend on their order, so the UN partial sums of a lane group are
+            // reduced by a reduce-scatter: each exchange with the partner lane halves the values a
+            // lane holds, and lane `sub` ends with the totals of candidates base .. base + cnt - 1
+            // (log2 UN shuffles per lane instead of UN * log2 lpv).
+            T s[UN];
 #pragma unroll
-        for (int u = 0; u < UN; u++) {
-            if (c0 + ngrp * u >= nc) break;  // warp-uniform
-            T s = 0;
+            for (int u = 0; u < UN; u++) {
+                s[u] = 0;
 #pragma unroll
-            for (int k = 0; k < CPL; k++) {
-                if (a.metric == MET_L2) Acc<DT>::l2(s, q[k], v[u][k]);
-                else Acc<DT>::ip(s, q[k], v[u][k]);
+                for (int k = 0; k < CPL; k++) {
+                    if (a.metric == MET_L2) Acc<DT>::l2(s[u], q[k], v[u][k]);
+                    else Acc<DT>::ip(s[u], q[k], v[u][k]);
+                }
             }
-            s = group_sum(s, lpv);
-            int c = c0 + grp + ngrp * u;
-            if (sub == 0 && c < nc) ckey[c] = make_key(finish_dk(s, a.metric), cid[c]);
+            int base = 0, m = lpv >> 1;
+#pragma unroll
+            for (int hh = UN >> 1; hh >= 1; hh >>= 1) {
+                if (m >= 1) {  // warp-uniform
+                    const bool up = (sub & m) != 0;
+#pragma unroll
+                    for (int i = 0; i < hh; i++) {
+                        const T send = up ? s[i] : s[i + hh];
+                        const T keep = up ? s[i + hh] : s[i];
+                        s[i] = keep + __shfl_xor_sync(0xffffffffu, send, m);
+                    }
+                    if (up) base += hh;
+                    m >>= 1;
+                }
+            }
+            for (; m >= 1; m >>= 1) s[0] += __shfl_xor_sync(0xffffffffu, s[0], m);  // lpv > UN
+            const int cnt = lpv >= UN ? 1 : UN / lpv;
+            const bool writer = lpv <= UN || (sub & (lpv / UN - 1)) == 0;
+#pragma unroll
+            for (int i = 0; i < UN; i++) {
+                if (i >= cnt) break;  // warp-uniform
+                const int c = c0 + grp + ngrp * (base + i);
+                if (writer && c < nc) ckey[c] = make_key(finish_dk(s[i], a.metric), cid[c]);
+            }
+        } else {
+            // fp32: one fixed summation tree (the one eval_one uses), so an id evaluated twice gets
+            // the same key
+#pragma unroll
+            for (int u = 0; u < UN; u++) {
+                if (c0 + ngrp * u >= nc) break;  // warp-uniform
+                T s = 0;
+#pragma unroll
+                for (int k = 0; k < CPL; k++) {
+                    if (a.metric == MET_L2) Acc<DT>::l2(s, q[k], v[u][k]);
+                    else Acc<DT>::ip(s, q[k], v[u][k]);
+                }
+                s = group_sum(s, lpv);
+                int c = c0 + grp + ngrp * u;
+                if (sub == 0 && c < nc) ckey[c] = make_key(finish_dk(s, a.metric), cid[c]);
+            }
         }
     }
 }
