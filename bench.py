@@ -300,6 +300,65 @@ def run_serve(args, cfg, ds, rr, gi, stream, dev):
     print(json.dumps(line), flush=True)
 
 
+def run_experiments(args, cfg, ds, rr, gi, stream, dev):
+    """Where time goes per phase, per variant (the paper's phase breakdown, Sec. 5), and how QPS, result
+    volume and AP move with the radius (its radius sweep), from the library's own per-phase events."""
+    import torch
+    Qd = torch.from_numpy(ds.Q).to("cuda:%d" % dev)
+    nq, n = len(ds.Q), ds.X.shape[0]
+    beam = args.exp_beam
+    phases = []
+    for variant in VARIANTS:
+        p = rr.rr_params_init(beam=beam, profile=1)
+        for _ in range(2):
+            st, res = rr.rr_range_search(gi.h, Qd, ds.radius, variant, p, stream=stream.cuda_stream,
+                                         result_on_device=True)
+            rr.rr_result_free(res)
+        acc = {"beam_ms": 0.0, "phase2_ms": 0.0, "output_ms": 0.0, "total_ms": 0.0}
+        reps = 5
+        for _ in range(reps):
+            st, res = rr.rr_range_search(gi.h, Qd, ds.radius, variant, p, stream=stream.cuda_stream,
+                                         result_on_device=True)
+            rr.rr_result_free(res)
+            prof = rr.rr_last_profile(gi.h)
+            for k in acc:
+                acc[k] += getattr(prof, k) / reps
+        row = {"variant": variant, "beam": beam, **{k: round(v, 4) for k, v in acc.items()},
+               "phase2_steps": prof.phase2_steps, "phase2_queries": prof.phase2_queries}
+        phases.append(row)
+        log("phases %-12s b=%d: beam %.3f ms, phase 2 %.3f ms (%d steps, %d queries), output %.3f ms" % (
+            variant, beam, acc["beam_ms"], acc["phase2_ms"], prof.phase2_steps, prof.phase2_queries,
+            acc["output_ms"]))
+    sweep = []
+    for mult in [float(x) for x in args.exp_radii.split(",")]:
+        r = ds.radius * mult
+        if ds.X.dtype != np.float32:
+            r = float(np.floor(r))
+        gt = gi.brute_force(Qd, r)
+        truth = csr_keys(gt.offsets, gt.ids, n)
+        for variant in ("greedy", "greedy_es"):
+            p = rr.rr_params_init(beam=beam, max_results_total=1 << 30)
+            st, res = rr.rr_range_search(gi.h, Qd, r, variant, p, stream=stream.cuda_stream, result_on_device=False)
+            rres = rr.RangeResult(res, st)
+            apv = average_precision(truth, rres, n)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(3):
+                st, res = rr.rr_range_search(gi.h, Qd, r, variant, p, stream=stream.cuda_stream, result_on_device=True)
+                rr.rr_result_free(res)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / 3
+            row = {"radius_over_r": mult, "variant": variant, "beam": beam, "qps": nq / (ms / 1000), "ap": apv,
+                   "results": int(len(rres.ids)), "zero_result_frac": float(np.mean(np.diff(gt.offsets) == 0))}
+            sweep.append(row)
+            log("radius %.2fr %-10s b=%d: %.0f QPS, AP %.4f, %d results, %.3f of queries match nothing" % (
+                mult, variant, beam, row["qps"], apv, row["results"], row["zero_result_frac"]))
+    print(json.dumps({"metric": "phase breakdown and radius sweep", "config": {"workload": cfg.name, "beam": beam},
+                      "phases": phases, "radius_sweep": sweep}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -325,6 +384,9 @@ def main():
     ap.add_argument("--serve-max-batch", type=int, default=4096)
     ap.add_argument("--serve-wait-us", type=int, default=100)
     ap.add_argument("--serve-device", type=int, default=1, choices=[0, 1], help="serving results in device memory")
+    ap.add_argument("--experiments", action="store_true", help="phase breakdown per variant and a radius sweep")
+    ap.add_argument("--exp-beam", type=int, default=64)
+    ap.add_argument("--exp-radii", default="0.5,0.75,1.0,1.5,2.0")
     args = ap.parse_args()
 
     ws, rank, local = dist_env()
@@ -354,6 +416,10 @@ def main():
     if args.serve:
         if rank == 0:
             run_serve(args, cfg, ds, rr, gi, stream, dev)
+        return
+    if args.experiments:
+        if rank == 0:
+            run_experiments(args, cfg, ds, rr, gi, stream, dev)
         return
     Qd = torch.from_numpy(ds.Q).to("cuda:%d" % dev)
     nq = Qd.shape[0]
