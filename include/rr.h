@@ -318,6 +318,11 @@ rr_status rr_serve_destroy(rr_server *srv);
  * Waits for the stream a device result is ordered on. */
 rr_status rr_result_to_host(const rr_result *result, rr_result *host);
 
+/* sizeof of the public structs, for bindings to check their layouts against:
+ * out[0..6] = rr_params, rr_query_stats, rr_result, rr_index_info, rr_profile,
+ * rr_serve_cfg, rr_serve_stats_t.  Needs no GPU. */
+void rr_abi_sizes(int64_t out[7]);
+
 /* Free the arrays of a result (host or device) and zero the struct. */
 rr_status rr_result_free(rr_result *result);
 

@@ -33,7 +33,8 @@ RR_FLAG_TRUNCATED, RR_FLAG_EARLY_STOPPED, RR_FLAG_PHASE2, RR_FLAG_CANCELED = 1, 
 EXPORTS = ["rr_params_init", "rr_create_index", "rr_load_index", "rr_free_index", "rr_index_info_get",
            "rr_range_search", "rr_brute_force", "rr_result_free", "rr_last_error", "rr_last_profile",
            "rr_beam_search_noalloc", "rr_serve_cfg_init", "rr_serve_create", "rr_serve_submit", "rr_serve_poll",
-           "rr_serve_collect", "rr_serve_cancel", "rr_serve_stats", "rr_serve_destroy", "rr_result_to_host"]
+           "rr_serve_collect", "rr_serve_cancel", "rr_serve_stats", "rr_serve_destroy", "rr_result_to_host",
+           "rr_abi_sizes"]
 
 
 class RRError(RuntimeError):
@@ -148,6 +149,8 @@ def load_library(path: str | None = None):
     L.rr_serve_cancel.argtypes = [P]
     L.rr_result_to_host.restype = ctypes.c_int
     L.rr_result_to_host.argtypes = [P, P]
+    L.rr_abi_sizes.restype = None
+    L.rr_abi_sizes.argtypes = [P]
     L.rr_serve_stats.restype = ctypes.c_int
     L.rr_serve_stats.argtypes = [P, P, I32]
     L.rr_serve_destroy.restype = ctypes.c_int
@@ -164,6 +167,15 @@ def _check(status):
 # ------------------------------------------------------------------------------------------------
 # one-to-one entry points
 # ------------------------------------------------------------------------------------------------
+
+def rr_abi_sizes() -> dict:
+    """sizeof of the public C structs as the library was compiled (layout check for this binding)."""
+    out = (ctypes.c_int64 * 7)()
+    load_library().rr_abi_sizes(out)
+    names = ["rr_params", "rr_query_stats", "rr_result", "rr_index_info", "rr_profile", "rr_serve_cfg",
+             "rr_serve_stats_t"]
+    return dict(zip(names, list(out)))
+
 
 def rr_last_error() -> str:
     return load_library().rr_last_error().decode("utf8", "replace")

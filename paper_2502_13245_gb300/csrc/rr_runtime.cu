@@ -300,6 +300,17 @@ rr_status rr_index_info_get(const rr_index *ix, rr_index_info *info) {
     return RR_OK;
 }
 
+void rr_abi_sizes(int64_t out[7]) {
+    if (!out) return;
+    out[0] = sizeof(rr_params);
+    out[1] = sizeof(rr_query_stats);
+    out[2] = sizeof(rr_result);
+    out[3] = sizeof(rr_index_info);
+    out[4] = sizeof(rr_profile);
+    out[5] = sizeof(rr_serve_cfg);
+    out[6] = sizeof(rr_serve_stats_t);
+}
+
 rr_status rr_result_to_host(const rr_result *r, rr_result *h) {
     if (!r || !h) { set_error("rr_result_to_host: NULL argument"); return RR_EINVAL; }
     memset(h, 0, sizeof *h);

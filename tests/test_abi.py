@@ -68,3 +68,16 @@ def test_rrx_reader_rejects_corrupt_file(tmp_path):
     assert "checksum" in rr.rr_last_error()
     (tmp_path / "short.rrx").write_bytes(bytes(raw[:100]))
     assert L.rr_load_index(str(tmp_path / "short.rrx").encode(), 0, ctypes.byref(h)) == rr.RR_EFORMAT
+
+
+def test_binding_struct_layouts_match_the_library():
+    # every ctypes mirror of a public struct has the size the C compiler gave it
+    import paper_2502_13245_gb300 as rr
+    rr.build()
+    sizes = rr.rr_abi_sizes()
+    mirror = {"rr_params": rr.Params, "rr_query_stats": rr.QueryStats, "rr_result": rr.Result,
+              "rr_index_info": rr.IndexInfo, "rr_profile": rr.Profile, "rr_serve_cfg": rr.ServeCfg,
+              "rr_serve_stats_t": rr.ServeStats}
+    for name, cls in mirror.items():
+        assert ctypes.sizeof(cls) == sizes[name], (name, ctypes.sizeof(cls), sizes[name])
+    assert rr.STATS_DTYPE.itemsize == sizes["rr_query_stats"]
