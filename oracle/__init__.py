@@ -46,7 +46,8 @@ class _Index(ctypes.Structure):
 
 class _Params(ctypes.Structure):
     _fields_ = [("variant", ctypes.c_int32), ("beam", ctypes.c_int32), ("b_max", ctypes.c_int32),
-                ("es_vl", ctypes.c_int32), ("es_radius", ctypes.c_double)]
+                ("es_vl", ctypes.c_int32), ("es_radius", ctypes.c_double), ("es_metric", ctypes.c_int32),
+                ("pad", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):
@@ -72,7 +73,7 @@ def _L():
         lib.or_range_search_one.argtypes = [P, P, ctypes.c_double, P, P, P, ctypes.c_int64, P]
         lib.or_beam_search.restype = ctypes.c_int
         lib.or_beam_search.argtypes = [P, P, P, ctypes.c_int64, ctypes.c_double, ctypes.c_int64, ctypes.c_int,
-                                       ctypes.c_int32, ctypes.c_double, P, P, P, P, P, P]
+                                       ctypes.c_int32, ctypes.c_double, ctypes.c_int32, P, P, P, P, P, P]
         lib.or_greedy_search.restype = ctypes.c_int64
         lib.or_greedy_search.argtypes = [P, P, P, ctypes.c_int64, ctypes.c_double, P, P, P]
         lib.or_brute_force.restype = ctypes.c_int64
@@ -113,11 +114,15 @@ class Index:
         return q
 
 
-def range_search_one(idx: Index, q, r, variant="greedy_es", beam=64, b_max=32768, es_vl=20, es_radius=None):
+ES_METRICS = {"visited": 0, "top1": 1, "top10": 2, "top10_ratio": 3}
+
+
+def range_search_one(idx: Index, q, r, variant="greedy_es", beam=64, b_max=32768, es_vl=20, es_radius=None,
+                     es_metric="visited"):
     """One query through Alg. 6 / Alg. 3 / plain beam search.  Returns (ids, dists, stats dict)."""
     q = idx._q(q)
     v = VARIANTS[variant] if isinstance(variant, str) else int(variant)
-    p = _Params(v, beam, b_max, es_vl, float(r if es_radius is None else es_radius))
+    p = _Params(v, beam, b_max, es_vl, float(r if es_radius is None else es_radius), ES_METRICS[es_metric])
     st = Stats()
     cap = 1024
     while True:
@@ -133,10 +138,12 @@ def range_search_one(idx: Index, q, r, variant="greedy_es", beam=64, b_max=32768
 
 
 def range_search(idx: Index, Q, r, variant="greedy_es", beam=64, b_max=32768, es_vl=20, es_radius=None,
-                 threads=1):
+                 threads=1, es_metric="visited"):
     """Batch driver (Alg. 6's parallel for; threads=1 is the single-threaded judge).
 
-    r: scalar or per-query array.  es_radius None means esr = r per query.
+    r: scalar or per-query array.  es_radius None means esr = r per query.  es_metric: the early-stopping
+    metric M of Alg. 4 -- "visited" (Alg. 5), "top1", "top10" (thresholds in distance units, es_radius) or
+    "top10_ratio" (d_top10 / d_start against the ratio es_radius).
     Returns (list of id arrays, list of dist arrays, list of stats dicts)."""
     Q = np.ascontiguousarray(Q, dtype=idx.X.dtype)
     nq = Q.shape[0]
@@ -146,11 +153,11 @@ def range_search(idx: Index, Q, r, variant="greedy_es", beam=64, b_max=32768, es
         ids, ds, sts = [], [], []
         esr = np.broadcast_to(np.asarray(es_radius, dtype=np.float64), (nq,))
         for i in range(nq):
-            a, b, s = range_search_one(idx, Q[i], radii[i], variant, beam, b_max, es_vl, esr[i])
+            a, b, s = range_search_one(idx, Q[i], radii[i], variant, beam, b_max, es_vl, esr[i], es_metric)
             ids.append(a); ds.append(b); sts.append(s)
         return ids, ds, sts
     v = VARIANTS[variant] if isinstance(variant, str) else int(variant)
-    p = _Params(v, beam, b_max, es_vl, float("nan"))
+    p = _Params(v, beam, b_max, es_vl, float("nan"), ES_METRICS[es_metric])
     # esr = r per query: the C batch driver reads es_radius from params, so run per distinct radius
     out_ids, out_d, out_s = [None] * nq, [None] * nq, [None] * nq
     for rv in np.unique(radii):
@@ -182,7 +189,7 @@ def range_search(idx: Index, Q, r, variant="greedy_es", beam=64, b_max=32768, es
     return out_ids, out_d, out_s
 
 
-def beam_search(idx: Index, q, S, r, b, use_es=False, es_vl=20, es_radius=None):
+def beam_search(idx: Index, q, S, r, b, use_es=False, es_vl=20, es_radius=None, es_metric="visited"):
     """Alg. 1 (+ Alg. 5 when use_es).  Returns (B ids sorted, B dists, V ids in visit order, stopped, stats)."""
     q = idx._q(q)
     S = np.ascontiguousarray(S, dtype=np.uint32)
@@ -195,7 +202,7 @@ def beam_search(idx: Index, q, S, r, b, use_es=False, es_vl=20, es_radius=None):
     st = Stats()
     esr = float(r if es_radius is None else es_radius)
     rc = _L().or_beam_search(ctypes.byref(idx._s), q.ctypes.data, S.ctypes.data, len(S), float(r), int(b),
-                             int(bool(use_es)), int(es_vl), esr, bi.ctypes.data, bd.ctypes.data, ctypes.byref(nB),
+                             int(bool(use_es)), int(es_vl), esr, ES_METRICS[es_metric], bi.ctypes.data, bd.ctypes.data, ctypes.byref(nB),
                              vi.ctypes.data, ctypes.byref(nV), ctypes.byref(st))
     if rc < 0:
         raise MemoryError("oracle allocation failed")

@@ -9,7 +9,8 @@
  * It follows "Range Retrieval with Graph-Based Indices" (arXiv 2502.13245):
  *   Def. 2.1 (range search), Def. 2.2 (average precision),
  *   Alg. 1 BeamSearch, Alg. 2 GreedySearch, Alg. 3 DoublingSearch,
- *   Alg. 4/5 EarlyStopping with the d_visited metric,
+ *   Alg. 4/5 EarlyStopping with the d_visited metric, and with the other
+ *            metrics of Sec. 3.2 (d_top1, d_top10, d_top10 / d_start),
  *   Alg. 6 GreedyRangeSearch (the per-query driver).
  * Readings where the paper is silent or garbled:
  *   - every argmin / "closest" / trim orders by the pair (distance, id);
@@ -17,6 +18,11 @@
  *   - Alg. 5 stops iff  min_{p in B} d(p,q) > r  and  |V| >= vl  and
  *     d(p*,q) > esr, tested for the candidate p* before it joins V; on a stop
  *     BeamSearch returns the current (B, V);
+ *   - the other metrics replace the last test of Alg. 5 (Alg. 4 with that M):
+ *     d_top1 = d of the closest point of B, d_top10 = d of the 10th closest
+ *     (the farthest one while |B| < 10), both against esr; d_top10 / d_start
+ *     against a ratio t, written d_top10 > t * d_start with d_start the
+ *     distance to the graph's start point (squared L2: distances >= 0);
  *   - Alg. 3 restarts every round from B = S, V = {} and continues iff
  *     |N| = b (lambda = 1); the beam never exceeds b_max: when doubling would
  *     pass b_max the last round's N is returned and flagged truncated;
@@ -56,7 +62,9 @@ typedef struct {
     int32_t beam;        /* b (starting beam for doubling) */
     int32_t b_max;       /* doubling cap */
     int32_t es_vl;       /* Alg. 5 visit limit vl */
-    double es_radius;    /* Alg. 5 esr */
+    double es_radius;    /* Alg. 5 esr (the ratio t for the d_top10 / d_start metric) */
+    int32_t es_metric;   /* 0 d_visited, 1 d_top1, 2 d_top10, 3 d_top10 / d_start */
+    int32_t pad;
 } or_params;
 
 typedef struct {
@@ -125,14 +133,28 @@ static double eval(const or_index *I, const void *q, uint32_t id, marks *m, or_s
     return or_dist(I, q, id);
 }
 
+/* ---------------------------------------------------------------- early-stopping metrics (Sec. 3.2)
+ * The metric M of Alg. 4, evaluated when p* (distance d_visit) is about to be
+ * visited; B is sorted and holds nb >= 1 points. */
+static int es_metric_exceeds(int metric, double d_visit, const ent *B, int64_t nb, double t, double d_start) {
+    const double d_top10 = B[(nb < 10 ? nb : 10) - 1].d;
+    switch (metric) {
+    case 1: return B[0].d > t;            /* d_top1 */
+    case 2: return d_top10 > t;           /* d_top10 */
+    case 3: return d_top10 > t * d_start; /* d_top10 / d_start > t */
+    default: return d_visit > t;          /* d_visited (Alg. 5) */
+    }
+}
+
 /* ---------------------------------------------------------------- Alg. 1 + Alg. 5
  * BeamSearch(q, G, P, S, r, b, M).  S is given with its distances (S_d).
  * On return B[0..*nB) is sorted by (dist, id) and V[0..*nV) lists the visited
  * points in visit order.  B must hold |S| + R entries, V must hold n.
- * use_es selects M = Alg. 5 (else M is never true).  Returns 1 if M fired. */
+ * use_es selects M = Alg. 5 with the given metric (else M is never true);
+ * d_start is q's distance to the graph's start point.  Returns 1 if M fired. */
 static int beam_search(const or_index *I, const void *q, const ent *S, int64_t nS, double r, int64_t b,
-                       int use_es, int32_t vl, double esr, ent *B, int64_t *nB, uint32_t *V, int64_t *nV,
-                       marks *m, or_stats *st) {
+                       int use_es, int32_t vl, double esr, int es_metric, double d_start, ent *B, int64_t *nB,
+                       uint32_t *V, int64_t *nV, marks *m, or_stats *st) {
     int64_t nb = 0, nv = 0;
     int stopped = 0;
     /* B <- S, V <- {} */
@@ -149,8 +171,11 @@ static int beam_search(const or_index *I, const void *q, const ent *S, int64_t n
             if (!m->inV[B[i].id]) { ip = i; break; }
         if (ip < 0) break; /* B \ V is empty */
         ent ps = B[ip];
-        /* early stopping, Alg. 5: closest point of B outside r, enough visits, p* outside esr */
-        if (use_es && B[0].d > r && nv >= vl && ps.d > esr) { stopped = 1; break; }
+        /* early stopping, Alg. 5: closest point of B outside r, enough visits, M above its threshold */
+        if (use_es && B[0].d > r && nv >= vl && es_metric_exceeds(es_metric, ps.d, B, nb, esr, d_start)) {
+            stopped = 1;
+            break;
+        }
         /* V <- V u {p*} */
         m->inV[ps.id] = 1;
         V[nv++] = ps.id;
@@ -257,11 +282,13 @@ int64_t or_range_search_one(const or_index *I, const void *q, double r, const or
     int64_t nS = 1, nres = 0;
     S[0].id = (uint32_t)I->start;
     S[0].d = eval(I, q, (uint32_t)I->start, &m, st);
+    const double d_start = S[0].d;
     inS[I->start] = 1;
     int first = 1;
     for (;;) {
         int64_t nB = 0, nV = 0;
-        int stopped = beam_search(I, q, S, nS, r, b, use_es, P->es_vl, P->es_radius, B, &nB, V, &nV, &m, st);
+        int stopped = beam_search(I, q, S, nS, r, b, use_es, P->es_vl, P->es_radius, P->es_metric, d_start, B, &nB,
+                                  V, &nV, &m, st);
         if (first) st->early_stopped = stopped;
         first = 0;
         st->final_beam = (int32_t)b;
@@ -308,7 +335,7 @@ int64_t or_range_search_one(const or_index *I, const void *q, double r, const or
  * Writes B (sorted) to b_ids/b_d (cap >= nS + R*n bound is the caller's job:
  * give n + R) and V in visit order.  Returns 1 if Alg. 5 fired, -1 on error. */
 int or_beam_search(const or_index *I, const void *q, const uint32_t *S_ids, int64_t nS, double r, int64_t b,
-                   int use_es, int32_t vl, double esr, uint32_t *b_ids, double *b_d, int64_t *nB,
+                   int use_es, int32_t vl, double esr, int32_t es_metric, uint32_t *b_ids, double *b_d, int64_t *nB,
                    uint32_t *v_ids, int64_t *nV, or_stats *st) {
     memset(st, 0, sizeof(*st));
     marks m;
@@ -317,7 +344,9 @@ int or_beam_search(const or_index *I, const void *q, const uint32_t *S_ids, int6
     ent *B = (ent *)malloc((size_t)(nS + I->n + I->R + 1) * sizeof(ent));
     if (!S || !B) { free(S); free(B); marks_free(&m); return -1; }
     for (int64_t i = 0; i < nS; i++) { S[i].id = S_ids[i]; S[i].d = eval(I, q, S_ids[i], &m, st); }
-    int stopped = beam_search(I, q, S, nS, r, b, use_es, vl, esr, B, nB, v_ids, nV, &m, st);
+    /* d_start: distance to the graph's start point (not an evaluation of the search) */
+    int stopped = beam_search(I, q, S, nS, r, b, use_es, vl, esr, es_metric, or_dist(I, q, (uint32_t)I->start), B,
+                              nB, v_ids, nV, &m, st);
     for (int64_t i = 0; i < *nB; i++) { b_ids[i] = B[i].id; b_d[i] = B[i].d; }
     free(S); free(B); marks_free(&m);
     return stopped;

@@ -272,3 +272,56 @@ def test_batch_threads_match_single(small):
     for x, y in zip(a[0], b[0]):
         assert np.array_equal(x, y)
     assert a[2] == b[2]
+
+
+# ---- early-stopping metrics of Sec. 3.2 (Alg. 4 with M = d_top1, d_top10, d_top10 / d_start)
+
+def _run_es(idx, ds, metric, t, variant="greedy_es", b=8, vl=5):
+    return oracle.range_search(idx, ds.Q, ds.radius, variant, beam=b, es_vl=vl, es_radius=t, es_metric=metric)
+
+
+def _same(a, b):
+    for x, y in zip(a[0], b[0]):
+        assert np.array_equal(x, y)
+    for s, u in zip(a[2], b[2]):
+        assert s == u
+
+
+def test_es_top1_below_r_is_the_bare_closest_outside_r_test(small):
+    """d_top1 > t with t <= r adds nothing to min_B d > r, so the stop rule reduces to
+    'closest point outside r and vl visits' -- d_visited with an esr no distance is below."""
+    ds, idx = small
+    for t in (ds.radius, ds.radius / 3.0):
+        _same(_run_es(idx, ds, "top1", t), _run_es(idx, ds, "visited", -1e300))
+
+
+def test_es_ratio_at_zero_is_top10_at_zero(small):
+    """d_top10 / d_start > 0 and d_top10 > 0 agree for squared L2 (d_start > 0 on these queries)."""
+    ds, idx = small
+    _same(_run_es(idx, ds, "top10_ratio", 0.0), _run_es(idx, ds, "top10", 0.0))
+
+
+def test_es_top10_stops_no_later_than_top1(small):
+    """d_top10 >= d_top1 at every step, so with one threshold the d_top10 rule fires no later."""
+    ds, idx = small
+    t = float(np.median([d for d in oracle.range_search(idx, ds.Q, 1e300, "beam", beam=8)[1][0]]))
+    a = _run_es(idx, ds, "top10", t, variant="beam_es")
+    b = _run_es(idx, ds, "top1", t, variant="beam_es")
+    for sa, sb in zip(a[2], b[2]):
+        assert sa["visits_beam"] <= sb["visits_beam"]
+        assert sb["early_stopped"] <= sa["early_stopped"]
+
+
+@pytest.mark.parametrize("metric", ["visited", "top1", "top10", "top10_ratio"])
+def test_es_metrics_keep_full_result_or_nothing(small, small_runs, metric):
+    """Any M only acts while the closest point of B is outside r: each result equals the
+    search without early stopping, or is empty; an unreachable threshold never stops."""
+    ds, idx = small
+    t = 0.5 if metric == "top10_ratio" else ds.radius * 0.5
+    full = small_runs[("greedy", 8)]
+    es = _run_es(idx, ds, metric, t)
+    for x, y, s in zip(full[0], es[0], es[2]):
+        assert np.array_equal(x, y) or (len(y) == 0 and s["early_stopped"])
+    never = _run_es(idx, ds, metric, 1e300)
+    for x, y, s in zip(full[0], never[0], never[2]):
+        assert np.array_equal(x, y) and not s["early_stopped"]
