@@ -94,8 +94,23 @@ typedef struct {
     int32_t tile_hint;         /* warps per CTA for the beam kernel (0 = library choice) */
     int32_t profile;           /* 1: record per-phase device times, see rr_last_profile */
     int32_t seen_log2;         /* log2 slots of the beam kernel's seen table, 5..14 (0 = library choice) */
-    int32_t reserved[5];
+    int32_t es_metric;         /* the M of Alg. 4 (Sec. 3.2), see rr_es_metric; RR_ES_VISITED is Alg. 5 */
+    int32_t reserved[4];
 } rr_params;
+
+/* Early-stopping metrics (Sec. 3.2; Alg. 4 with this M replacing Alg. 5's last
+ * test).  The search stops when the closest point of B is outside r, |V| >= vl,
+ * and M exceeds its threshold:
+ *   RR_ES_VISITED      d(p*, q) > esr                      (Alg. 5, the default)
+ *   RR_ES_TOP1         d of the closest point of B > esr
+ *   RR_ES_TOP10        d of the 10th closest point of B (the farthest while
+ *                      |B| < 10) > esr
+ *   RR_ES_TOP10_RATIO  d_top10 > t * d(start, q), t = es_radius (es_radius_mode
+ *                      must be 1; squared L2 only)
+ * Beam and greedy variants take every metric; the doubling variants take
+ * RR_ES_VISITED only (RR_EINVAL otherwise); rr_beam_search_noalloc always uses
+ * RR_ES_VISITED. */
+typedef enum { RR_ES_VISITED = 0, RR_ES_TOP1 = 1, RR_ES_TOP10 = 2, RR_ES_TOP10_RATIO = 3 } rr_es_metric;
 
 /* Exact per-query counters (collect_stats = 1).  visits_* count |V| of the
  * algorithms; distinct counts the distinct ids whose distance was evaluated. */

@@ -27,6 +27,7 @@ VARIANTS = {"beam": RR_BEAM, "beam_es": RR_BEAM_ES, "doubling": RR_DOUBLING, "do
 RR_U8, RR_I8, RR_F32 = 0, 1, 2
 RR_L2, RR_IP = 0, 1
 RR_PREC_EXACT, RR_PREC_BF16, RR_PREC_FP8 = 0, 1, 2
+RR_ES_VISITED, RR_ES_TOP1, RR_ES_TOP10, RR_ES_TOP10_RATIO = 0, 1, 2, 3
 RR_FLAG_TRUNCATED, RR_FLAG_EARLY_STOPPED, RR_FLAG_PHASE2, RR_FLAG_CANCELED = 1, 2, 4, 8
 
 # every symbol include/rr.h declares (checked by the ABI test)
@@ -48,7 +49,8 @@ class Params(ctypes.Structure):
                 ("es_radius_mode", ctypes.c_int32), ("es_radius", ctypes.c_double), ("precision", ctypes.c_int32),
                 ("recheck_eps", ctypes.c_float), ("persistent", ctypes.c_int32), ("collect_stats", ctypes.c_int32),
                 ("max_results_total", ctypes.c_int64), ("tile_hint", ctypes.c_int32),
-                ("profile", ctypes.c_int32), ("seen_log2", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
+                ("profile", ctypes.c_int32), ("seen_log2", ctypes.c_int32), ("es_metric", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 4)]
 
 
 class Profile(ctypes.Structure):

@@ -151,8 +151,22 @@ __device__ __forceinline__ void search_query(const SearchArgs &a, int hlg, int64
     while (cur < nb) {
         // p* <- argmin over B \ V = B[cur] (B sorted, everything before cur visited)
         const uint64_t pk = B[cur];
-        // Alg. 5: closest of B outside r, |V| >= vl, d(p*) outside esr
-        if (a.use_es && key_dk(B[0]) > rks && nvis >= a.es_vl && key_dk(pk) > ek) { stopped = true; break; }
+        // Alg. 5 / Alg. 4: closest of B outside r, |V| >= vl, the metric above its threshold
+        if (a.use_es && key_dk(B[0]) > rks && nvis >= a.es_vl) {
+            bool fire;
+            const uint32_t d10 = key_dk(B[min(nb, 10) - 1]);
+            switch (a.es_metric) {
+            case RR_ES_TOP1: fire = key_dk(B[0]) > ek; break;
+            case RR_ES_TOP10: fire = d10 > ek; break;
+            case RR_ES_TOP10_RATIO: {
+                const bool fp = DT == DT_F32 || LP;
+                fire = dkey_value(d10, fp) > a.es_ratio * dkey_value(dk0, fp);
+                break;
+            }
+            default: fire = key_dk(pk) > ek;  // d_visited
+            }
+            if (fire) { stopped = true; break; }
+        }
         const uint32_t p = key_id(pk);
         if (++guard > a.n + 1 || p >= (uint32_t)a.n) {  // cannot happen for a validated index
             if (lane == 0) atomicExch(a.error, p >= (uint32_t)a.n ? 3 : 1);

@@ -32,6 +32,13 @@ __device__ __forceinline__ uint32_t dkey_f32(float f) {
 __device__ __forceinline__ float dval_f32(uint32_t k) {
     return __uint_as_float((k & 0x80000000u) ? (k & 0x7FFFFFFFu) : ~k);
 }
+// The distance an order key encodes (exact for int32 distances).
+__device__ __forceinline__ double dkey_value(uint32_t dk, bool fp) {
+    if (!fp) return (double)(int32_t)(dk ^ 0x80000000u);
+    const uint32_t b = (dk & 0x80000000u) ? (dk & 0x7fffffffu) : ~dk;
+    return (double)__uint_as_float(b);
+}
+
 __host__ __device__ __forceinline__ uint64_t make_key(uint32_t dk, uint32_t id) {
     return ((uint64_t)dk << 32) | ((uint64_t)id << 1);
 }

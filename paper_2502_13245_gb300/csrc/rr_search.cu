@@ -478,6 +478,19 @@ extern "C" rr_status rr_range_search(rr_index *ix, const void *queries, int64_t 
     const bool doubling = variant == RR_DOUBLING || variant == RR_DOUBLING_ES;
     const bool greedy = variant == RR_GREEDY || variant == RR_GREEDY_ES;
     const bool use_es = variant == RR_BEAM_ES || variant == RR_DOUBLING_ES || variant == RR_GREEDY_ES;
+    if (P.es_metric < RR_ES_VISITED || P.es_metric > RR_ES_TOP10_RATIO) {
+        set_error("rr_range_search: unknown early-stopping metric %d", P.es_metric);
+        return RR_EINVAL;
+    }
+    if (use_es && doubling && P.es_metric != RR_ES_VISITED) {
+        set_error("rr_range_search: the doubling variants stop early on d_visited only");
+        return RR_EINVAL;
+    }
+    if (use_es && P.es_metric == RR_ES_TOP10_RATIO && (P.es_radius_mode != 1 || ix->metric != RR_L2)) {
+        set_error("rr_range_search: the d_top10 / d_start metric takes its ratio from es_radius "
+                  "(es_radius_mode = 1) and needs squared L2");
+        return RR_EINVAL;
+    }
     if (doubling && P.b_max < P.beam) { set_error("rr_range_search: b_max < beam"); return RR_EINVAL; }
     DeviceGuard dg(ix->device);
     rr_status s = stage(S, queries, radii, radius, false);
@@ -485,6 +498,8 @@ extern "C" rr_status rr_range_search(rr_index *ix, const void *queries, int64_t 
     SearchArgs &a = S.a;
     a.use_es = use_es ? 1 : 0;
     a.es_vl = P.es_visit_limit;
+    a.es_metric = P.es_metric;
+    a.es_ratio = P.es_radius;
     a.hash_lg = P.seen_log2;
     a.persistent = P.persistent ? 1 : 0;
     a.next_q = a.p2_count + 2;  // zeroed with the other counters in stage()

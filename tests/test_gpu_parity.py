@@ -104,6 +104,34 @@ def test_launch_shapes_do_not_change_results(rr, c0, c0_index, c0_oracle, shape)
         assert_same(res, o_ids, o_d, len(c0.Q))
 
 
+@pytest.mark.parametrize("metric,thr", [("top1", 1.5), ("top10", 1.5), ("top10_ratio", 0.9), ("visited", 1.2)])
+@pytest.mark.parametrize("variant,beam", [("greedy_es", 16), ("beam_es", 32)])
+def test_c0_early_stop_metrics_bit_exact(rr, c0, c0_index, c0_oracle, metric, thr, variant, beam):
+    """Alg. 4 with the metrics of Sec. 3.2: same results, stop decisions and visit counts as the oracle."""
+    m = {"visited": rr.RR_ES_VISITED, "top1": rr.RR_ES_TOP1, "top10": rr.RR_ES_TOP10,
+         "top10_ratio": rr.RR_ES_TOP10_RATIO}[metric]
+    t = thr if metric == "top10_ratio" else float(np.floor(c0.radius * thr))
+    o_ids, o_d, o_st = oracle.range_search(c0_oracle, c0.Q, c0.radius, variant, beam=beam, es_vl=10, es_radius=t,
+                                           es_metric=metric, threads=os.cpu_count() or 4)
+    res = c0_index.range_search(c0.Q, c0.radius, variant, beam=beam, es_visit_limit=10, es_radius_mode=1,
+                                es_radius=t, es_metric=m, collect_stats=1)
+    assert res.status == rr.RR_OK
+    assert_same(res, o_ids, o_d, len(c0.Q))
+    es = np.array([s["early_stopped"] for s in o_st], bool)
+    assert np.array_equal((res.flags & rr.RR_FLAG_EARLY_STOPPED) != 0, es)
+    assert np.array_equal(res.stats["visits_beam"], [s["visits_beam"] for s in o_st])
+    assert es.any()  # the threshold makes the metric act on this workload
+
+
+def test_early_stop_metric_arguments_are_checked(rr, c0, c0_index):
+    for variant, kw in (("doubling_es", dict(es_metric=rr.RR_ES_TOP1)),
+                        ("greedy_es", dict(es_metric=rr.RR_ES_TOP10_RATIO)),  # ratio needs es_radius_mode = 1
+                        ("greedy_es", dict(es_metric=7))):
+        p = rr.rr_params_init(beam=16, **kw)
+        st, _ = rr.rr_range_search(c0_index.h, c0.Q[:4], c0.radius, variant, p, check=False)
+        assert st == rr.RR_EINVAL
+
+
 def test_ragged_and_tiny_batches(rr, c0, c0_index, c0_oracle):
     for nq in (1, 2, 37, 129):
         Q = c0.Q[:nq]
