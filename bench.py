@@ -355,8 +355,38 @@ def run_experiments(args, cfg, ds, rr, gi, stream, dev):
             sweep.append(row)
             log("radius %.2fr %-10s b=%d: %.0f QPS, AP %.4f, %d results, %.3f of queries match nothing" % (
                 mult, variant, beam, row["qps"], apv, row["results"], row["zero_result_frac"]))
-    print(json.dumps({"metric": "phase breakdown and radius sweep", "config": {"workload": cfg.name, "beam": beam},
-                      "phases": phases, "radius_sweep": sweep}), flush=True)
+    # early-stopping metrics of Sec. 3.2 (greedy_es): QPS, AP and the share of queries stopped early
+    gt = gi.brute_force(Qd, ds.radius)
+    truth = csr_keys(gt.offsets, gt.ids, n)
+    es_rows = []
+    for name, m, thrs in (("visited", rr.RR_ES_VISITED, (1.0, 1.5, 2.0)), ("top1", rr.RR_ES_TOP1, (1.0, 1.5, 2.0)),
+                          ("top10", rr.RR_ES_TOP10, (1.0, 1.5, 2.0)),
+                          ("top10_ratio", rr.RR_ES_TOP10_RATIO, (0.3, 0.5, 0.7))):
+        for t in thrs:
+            thr = t if name == "top10_ratio" else float(ds.radius) * t
+            p = rr.rr_params_init(beam=beam, es_visit_limit=20, es_radius_mode=1, es_radius=thr, es_metric=m)
+            st, res = rr.rr_range_search(gi.h, Qd, ds.radius, "greedy_es", p, stream=stream.cuda_stream,
+                                         result_on_device=False)
+            rres = rr.RangeResult(res, st)
+            apv = average_precision(truth, rres, n)
+            stopped = float(np.mean((rres.flags & rr.RR_FLAG_EARLY_STOPPED) != 0))
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(3):
+                st, res = rr.rr_range_search(gi.h, Qd, ds.radius, "greedy_es", p, stream=stream.cuda_stream,
+                                             result_on_device=True)
+                rr.rr_result_free(res)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / 3
+            row = {"metric": name, "threshold": t, "qps": nq / (ms / 1000), "ap": apv, "stopped": stopped}
+            es_rows.append(row)
+            log("es %-11s t=%.2f%s: %.0f QPS, AP %.4f, %.3f stopped early" % (
+                name, t, "" if name == "top10_ratio" else "r", row["qps"], apv, stopped))
+    print(json.dumps({"metric": "phase breakdown, radius sweep, early-stopping metrics",
+                      "config": {"workload": cfg.name, "beam": beam},
+                      "phases": phases, "radius_sweep": sweep, "early_stop_metrics": es_rows}), flush=True)
 
 
 def main():
