@@ -399,8 +399,8 @@ def main():
     ap.add_argument("--variants", default=",".join(VARIANTS))
     ap.add_argument("--beams", default=",".join(map(str, BEAMS)))
     ap.add_argument("--cpu-sample", type=int, default=0, help="queries for the cpu_baseline leg (0 = auto)")
-    ap.add_argument("--ref-variant", default="greedy_es")
-    ap.add_argument("--ref-beam", type=int, default=16)
+    ap.add_argument("--ref-variant", default="greedy", help="the form the GPU arm picks on C1 (AP >= 0.95)")
+    ap.add_argument("--ref-beam", type=int, default=192)
     ap.add_argument("--ref-sample", type=int, default=300)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--fixed", default="", help="VARIANT:BEAM[:VL:ESR] -- skip the sweep and time this form")
