@@ -47,7 +47,7 @@ class _Index(ctypes.Structure):
 class _Params(ctypes.Structure):
     _fields_ = [("variant", ctypes.c_int32), ("beam", ctypes.c_int32), ("b_max", ctypes.c_int32),
                 ("es_vl", ctypes.c_int32), ("es_radius", ctypes.c_double), ("es_metric", ctypes.c_int32),
-                ("pad", ctypes.c_int32)]
+                ("expand", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):
@@ -118,11 +118,11 @@ ES_METRICS = {"visited": 0, "top1": 1, "top10": 2, "top10_ratio": 3}
 
 
 def range_search_one(idx: Index, q, r, variant="greedy_es", beam=64, b_max=32768, es_vl=20, es_radius=None,
-                     es_metric="visited"):
+                     es_metric="visited", expand=1):
     """One query through Alg. 6 / Alg. 3 / plain beam search.  Returns (ids, dists, stats dict)."""
     q = idx._q(q)
     v = VARIANTS[variant] if isinstance(variant, str) else int(variant)
-    p = _Params(v, beam, b_max, es_vl, float(r if es_radius is None else es_radius), ES_METRICS[es_metric])
+    p = _Params(v, beam, b_max, es_vl, float(r if es_radius is None else es_radius), ES_METRICS[es_metric], expand)
     st = Stats()
     cap = 1024
     while True:
@@ -138,12 +138,13 @@ def range_search_one(idx: Index, q, r, variant="greedy_es", beam=64, b_max=32768
 
 
 def range_search(idx: Index, Q, r, variant="greedy_es", beam=64, b_max=32768, es_vl=20, es_radius=None,
-                 threads=1, es_metric="visited"):
+                 threads=1, es_metric="visited", expand=1):
     """Batch driver (Alg. 6's parallel for; threads=1 is the single-threaded judge).
 
     r: scalar or per-query array.  es_radius None means esr = r per query.  es_metric: the early-stopping
     metric M of Alg. 4 -- "visited" (Alg. 5), "top1", "top10" (thresholds in distance units, es_radius) or
-    "top10_ratio" (d_top10 / d_start against the ratio es_radius).
+    "top10_ratio" (d_top10 / d_start against the ratio es_radius).  expand > 1 selects the multi-parent
+    variant of Alg. 1 (that many closest unvisited points of B visited per iteration; not in the paper).
     Returns (list of id arrays, list of dist arrays, list of stats dicts)."""
     Q = np.ascontiguousarray(Q, dtype=idx.X.dtype)
     nq = Q.shape[0]
@@ -153,11 +154,11 @@ def range_search(idx: Index, Q, r, variant="greedy_es", beam=64, b_max=32768, es
         ids, ds, sts = [], [], []
         esr = np.broadcast_to(np.asarray(es_radius, dtype=np.float64), (nq,))
         for i in range(nq):
-            a, b, s = range_search_one(idx, Q[i], radii[i], variant, beam, b_max, es_vl, esr[i], es_metric)
+            a, b, s = range_search_one(idx, Q[i], radii[i], variant, beam, b_max, es_vl, esr[i], es_metric, expand)
             ids.append(a); ds.append(b); sts.append(s)
         return ids, ds, sts
     v = VARIANTS[variant] if isinstance(variant, str) else int(variant)
-    p = _Params(v, beam, b_max, es_vl, float("nan"), ES_METRICS[es_metric])
+    p = _Params(v, beam, b_max, es_vl, float("nan"), ES_METRICS[es_metric], expand)
     # esr = r per query: the C batch driver reads es_radius from params, so run per distinct radius
     out_ids, out_d, out_s = [None] * nq, [None] * nq, [None] * nq
     for rv in np.unique(radii):

@@ -64,7 +64,7 @@ typedef struct {
     int32_t es_vl;       /* Alg. 5 visit limit vl */
     double es_radius;    /* Alg. 5 esr (the ratio t for the d_top10 / d_start metric) */
     int32_t es_metric;   /* 0 d_visited, 1 d_top1, 2 d_top10, 3 d_top10 / d_start */
-    int32_t pad;
+    int32_t expand;      /* parents expanded per BeamSearch iteration (0 or 1: Alg. 1 itself) */
 } or_params;
 
 typedef struct {
@@ -151,10 +151,18 @@ static int es_metric_exceeds(int metric, double d_visit, const ent *B, int64_t n
  * On return B[0..*nB) is sorted by (dist, id) and V[0..*nV) lists the visited
  * points in visit order.  B must hold |S| + R entries, V must hold n.
  * use_es selects M = Alg. 5 with the given metric (else M is never true);
- * d_start is q's distance to the graph's start point.  Returns 1 if M fired. */
+ * d_start is q's distance to the graph's start point.  Returns 1 if M fired.
+ *
+ * expand > 1 (at most 64) is a variant of Alg. 1 that is not in the paper, a
+ * multi-parent beam search: each iteration visits the `expand` closest
+ * unvisited points of B at once (p* first; M is tested on p*), adds the
+ * out-neighbours of all of them not in V or B, in parent order, then trims to
+ * b once.  It trades a few extra visits for fewer, wider iterations (more
+ * independent gathers per step on a GPU).  expand = 1 is Alg. 1 exactly. */
 static int beam_search(const or_index *I, const void *q, const ent *S, int64_t nS, double r, int64_t b,
-                       int use_es, int32_t vl, double esr, int es_metric, double d_start, ent *B, int64_t *nB,
-                       uint32_t *V, int64_t *nV, marks *m, or_stats *st) {
+                       int use_es, int32_t vl, double esr, int es_metric, double d_start, int expand, ent *B,
+                       int64_t *nB, uint32_t *V, int64_t *nV, marks *m, or_stats *st) {
+    if (expand < 1) expand = 1;
     int64_t nb = 0, nv = 0;
     int stopped = 0;
     /* B <- S, V <- {} */
@@ -176,19 +184,28 @@ static int beam_search(const or_index *I, const void *q, const ent *S, int64_t n
             stopped = 1;
             break;
         }
-        /* V <- V u {p*} */
-        m->inV[ps.id] = 1;
-        V[nv++] = ps.id;
-        /* B <- B u (N_out(p*) \ V) */
-        const uint32_t *row = I->adj + (size_t)ps.id * I->R;
-        for (int k = 0; k < I->R; k++) {
-            uint32_t j = row[k];
-            if (j == OR_SENT) continue;
-            if (m->inV[j] || m->inB[j]) continue;
-            B[nb].id = j;
-            B[nb].d = eval(I, q, j, m, st);
-            m->inB[j] = 1;
-            nb++;
+        /* the parents of this iteration: p* and the next expand - 1 unvisited points of B */
+        uint32_t par[64];
+        int np = 0;
+        for (int64_t i = ip; i < nb && np < expand && np < 64; i++)
+            if (!m->inV[B[i].id]) par[np++] = B[i].id;
+        for (int e = 0; e < np; e++) {
+            /* V <- V u {p} */
+            m->inV[par[e]] = 1;
+            V[nv++] = par[e];
+        }
+        for (int e = 0; e < np; e++) {
+            /* B <- B u (N_out(p) \ V) */
+            const uint32_t *row = I->adj + (size_t)par[e] * I->R;
+            for (int k = 0; k < I->R; k++) {
+                uint32_t j = row[k];
+                if (j == OR_SENT) continue;
+                if (m->inV[j] || m->inB[j]) continue;
+                B[nb].id = j;
+                B[nb].d = eval(I, q, j, m, st);
+                m->inB[j] = 1;
+                nb++;
+            }
         }
         qsort(B, (size_t)nb, sizeof(ent), cmp_ent);
         /* if |B| > b, keep the b closest */
@@ -287,8 +304,8 @@ int64_t or_range_search_one(const or_index *I, const void *q, double r, const or
     int first = 1;
     for (;;) {
         int64_t nB = 0, nV = 0;
-        int stopped = beam_search(I, q, S, nS, r, b, use_es, P->es_vl, P->es_radius, P->es_metric, d_start, B, &nB,
-                                  V, &nV, &m, st);
+        int stopped = beam_search(I, q, S, nS, r, b, use_es, P->es_vl, P->es_radius, P->es_metric, d_start,
+                                  P->expand, B, &nB, V, &nV, &m, st);
         if (first) st->early_stopped = stopped;
         first = 0;
         st->final_beam = (int32_t)b;
@@ -345,8 +362,8 @@ int or_beam_search(const or_index *I, const void *q, const uint32_t *S_ids, int6
     if (!S || !B) { free(S); free(B); marks_free(&m); return -1; }
     for (int64_t i = 0; i < nS; i++) { S[i].id = S_ids[i]; S[i].d = eval(I, q, S_ids[i], &m, st); }
     /* d_start: distance to the graph's start point (not an evaluation of the search) */
-    int stopped = beam_search(I, q, S, nS, r, b, use_es, vl, esr, es_metric, or_dist(I, q, (uint32_t)I->start), B,
-                              nB, v_ids, nV, &m, st);
+    int stopped = beam_search(I, q, S, nS, r, b, use_es, vl, esr, es_metric, or_dist(I, q, (uint32_t)I->start), 1,
+                              B, nB, v_ids, nV, &m, st);
     for (int64_t i = 0; i < *nB; i++) { b_ids[i] = B[i].id; b_d[i] = B[i].d; }
     free(S); free(B); marks_free(&m);
     return stopped;

@@ -325,3 +325,48 @@ def test_es_metrics_keep_full_result_or_nothing(small, small_runs, metric):
     never = _run_es(idx, ds, metric, 1e300)
     for x, y, s in zip(full[0], never[0], never[2]):
         assert np.array_equal(x, y) and not s["early_stopped"]
+
+
+# ---- multi-parent beam search (expand parents per iteration; a variant of Alg. 1, not in the paper)
+
+@pytest.mark.parametrize("expand", [2, 4])
+@pytest.mark.parametrize("variant", ["beam", "greedy"])
+def test_multi_parent_exhaustive_equals_brute_force(tiny, variant, expand):
+    """With b >= n on a graph where every point is reachable, any number of parents per iteration
+    still visits everything, so the result is the exact range (Def. 2.1)."""
+    ds, idx = tiny
+    assert _reachable(ds.adj, ds.start).all()
+    n = ds.X.shape[0]
+    for qi in range(len(ds.Q)):
+        ids, d, st = oracle.range_search_one(idx, ds.Q[qi], ds.radius, variant, beam=n, b_max=n, expand=expand)
+        eids, ed = _exact(ds, ds.Q[qi], ds.radius)
+        assert np.array_equal(ids, eids) and np.array_equal(d.astype(np.int64), ed)
+
+
+def test_multi_parent_with_one_parent_is_alg1(small, small_runs):
+    ds, idx = small
+    for v in ("beam_es", "greedy"):
+        a = oracle.range_search(idx, ds.Q, ds.radius, v, beam=8, b_max=4096, expand=1)
+        b = small_runs[(v, 8)]
+        for x, y in zip(a[0], b[0]):
+            assert np.array_equal(x, y)
+        assert [s["visits_beam"] for s in a[2]] == [s["visits_beam"] for s in b[2]]
+
+
+@pytest.mark.parametrize("expand", [2, 3, 8])
+def test_multi_parent_invariants(small, small_runs, expand):
+    """Results are in range, unique, sorted and exact-distance; plain beam keeps at most b; the early
+    stop still returns the full result or nothing."""
+    ds, idx = small
+    for v in ("beam", "greedy", "greedy_es"):
+        ids_l, d_l, st_l = oracle.range_search(idx, ds.Q, ds.radius, v, beam=16, expand=expand)
+        for qi, (ids, d, st) in enumerate(zip(ids_l, d_l, st_l)):
+            eids, ed = _exact(ds, ds.Q[qi], ds.radius)
+            assert np.all(np.isin(ids, eids)) and len(np.unique(ids)) == len(ids)
+            assert np.array_equal(np.lexsort((ids, d)), np.arange(len(ids)))
+            ex = dict(zip(eids.tolist(), ed.tolist()))
+            assert all(ex[i] == dd for i, dd in zip(ids.tolist(), d.tolist()))
+            if v == "beam":
+                assert len(ids) <= 16
+            if v == "greedy_es" and st["early_stopped"]:
+                assert len(ids) == 0
