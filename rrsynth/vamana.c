@@ -116,6 +116,14 @@ static int build_search(const ds_t *D, const uint32_t *adj, const int32_t *deg, 
         if (nv < maxv) { vis[nv] = p; vd[nv] = beam[i].d; nv++; }
         cur = i + 1;
         const uint32_t *row = adj + (size_t)p * R;
+        /* ask for the unseen neighbours' vectors first: their cache misses then overlap instead of
+         * arriving one distance at a time (a hint only; the search is unchanged) */
+        for (int k = 0; k < deg[p]; k++) {
+            uint32_t j = row[k];
+            if (stamp[j] == tag) continue;
+            const char *v = (const char *)vec(D, j);
+            for (size_t o = 0; o < D->row; o += 64) __builtin_prefetch(v + o, 0, 1);
+        }
         for (int k = 0; k < deg[p]; k++) {
             uint32_t j = row[k];
             if (stamp[j] == tag) continue;
