@@ -1,0 +1,39 @@
+"""The benchmark's average precision (Def. 2.2 over CSR results, as (query, id) keys) equals the
+oracle's definition on random result sets, including empty queries and queries with no truth."""
+import importlib.util
+import os
+
+import numpy as np
+
+import oracle
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _bench():
+    spec = importlib.util.spec_from_file_location("bench_mod", os.path.join(ROOT, "bench.py"))
+    m = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(m)
+    return m
+
+
+class _Res:
+    def __init__(self, lists):
+        self.offsets = np.concatenate([[0], np.cumsum([len(x) for x in lists])]).astype(np.int64)
+        self.ids = np.concatenate(lists).astype(np.uint32) if lists else np.zeros(0, np.uint32)
+
+
+def test_bench_ap_matches_definition():
+    b = _bench()
+    rng = np.random.default_rng(0)
+    n = 5000
+    for trial in range(20):
+        nq = int(rng.integers(1, 40))
+        truth = [np.sort(rng.choice(n, int(rng.integers(0, 30)), replace=False)) for _ in range(nq)]
+        found = []
+        for t in truth:
+            keep = t[rng.random(len(t)) < rng.random()]  # a subset of the true set
+            found.append(np.sort(keep))
+        tk = b.csr_keys(_Res(truth).offsets, _Res(truth).ids, n)
+        got = b.average_precision(tk, _Res(found), n)
+        assert abs(got - oracle.average_precision(truth, found)) < 1e-12
