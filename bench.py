@@ -227,7 +227,7 @@ def run_serve(args, cfg, ds, rr, gi, stream, dev):
         lock = threading.Condition()
         done = {"gen": False}
         lag = []
-        collected = [0, 0, 0]  # requests served, their results, requests canceled
+        collected = [0, 0]  # requests collected, their results
         t_last = [0.0]
 
         def collector():
