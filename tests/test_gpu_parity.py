@@ -184,9 +184,6 @@ def test_device_results(rr, c0, c0_index, c0_oracle):
     assert st == rr.RR_OK and res.on_device == 1
     torch.cuda.synchronize()
     nq, tot = res.nq, res.total
-    off = torch.empty(nq + 1, dtype=torch.int64, device="cuda")
-    ids = torch.empty(max(tot, 1), dtype=torch.int32, device="cuda")
-    cudart = ctypes.CDLL("libcudart.so") if False else None  # noqa: F841 (copies go through torch below)
     # wrap the device arrays with torch through __cuda_array_interface__
     class _A:
         def __init__(self, ptr, n, typestr):
