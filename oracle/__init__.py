@@ -21,9 +21,11 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 _SO = os.path.join(HERE, "_oracle.so")
 
-BEAM, BEAM_ES, DOUBLING, DOUBLING_ES, GREEDY, GREEDY_ES = range(6)
+BEAM, BEAM_ES, DOUBLING, DOUBLING_ES, GREEDY, GREEDY_ES, DOUBLING_WARM, DOUBLING_WARM_ES = range(8)
+# doubling_warm(_es): a variant of Alg. 3 that continues each round from the last instead of restarting
 VARIANTS = {"beam": BEAM, "beam_es": BEAM_ES, "doubling": DOUBLING, "doubling_es": DOUBLING_ES,
-            "greedy": GREEDY, "greedy_es": GREEDY_ES}
+            "greedy": GREEDY, "greedy_es": GREEDY_ES, "doubling_warm": DOUBLING_WARM,
+            "doubling_warm_es": DOUBLING_WARM_ES}
 U8, I8, F32 = 0, 1, 2
 L2, IP = 0, 1
 

@@ -44,7 +44,8 @@
 
 enum { OR_U8 = 0, OR_I8 = 1, OR_F32 = 2 };
 enum { OR_L2 = 0, OR_IP = 1 };
-enum { OR_BEAM = 0, OR_BEAM_ES = 1, OR_DOUBLING = 2, OR_DOUBLING_ES = 3, OR_GREEDY = 4, OR_GREEDY_ES = 5 };
+enum { OR_BEAM = 0, OR_BEAM_ES = 1, OR_DOUBLING = 2, OR_DOUBLING_ES = 3, OR_GREEDY = 4, OR_GREEDY_ES = 5,
+       OR_DOUBLING_WARM = 6, OR_DOUBLING_WARM_ES = 7 };
 
 typedef struct {
     const void *X;       /* n x d row-major */
@@ -275,12 +276,112 @@ static int64_t greedy_search(const or_index *I, const void *q, const ent *S, int
  * sorted by (dist, id).  Returns the number of results, or -1 on allocation
  * failure.  If the count exceeds cap, nothing is written past cap and the
  * caller should retry with a larger buffer. */
+/* ---------------------------------------------------------------- warm-restart doubling
+ * A variant of Alg. 3 that is not in the paper: instead of restarting every
+ * round from B = S with V = {} (which re-visits and re-evaluates), a round
+ * continues the previous one.  E is every point whose distance has been
+ * evaluated (with that distance) and V the visited points, both kept across
+ * rounds.  A round with beam b starts from B = the b closest points of E and
+ * runs Alg. 1's loop without visiting any point of V again (a neighbour
+ * already in E re-enters B with its stored distance, no new evaluation);
+ * N = {n in B : d <= r}; the search stops when |N| < b, else b doubles (capped
+ * by b_max as in Alg. 3, the last N flagged truncated).  The first round is
+ * Alg. 1 from the start point, as in Alg. 3.  Alg. 5 applies in every round.
+ * Writes N (sorted) to res; returns |N|, or -1 on allocation failure. */
+static int64_t warm_doubling(const or_index *I, const void *q, double r, const or_params *P, int use_es,
+                             ent *res, marks *m, or_stats *st) {
+    const int64_t n = I->n;
+    ent *E = (ent *)malloc((size_t)n * sizeof(ent));
+    ent *B = (ent *)malloc((size_t)(n + I->R + 1) * sizeof(ent));
+    double *ed = (double *)malloc((size_t)n * sizeof(double));
+    if (!E || !B || !ed) { free(E); free(B); free(ed); return -1; }
+    int64_t nE = 0, nv = 0, nres = 0;
+    ed[I->start] = eval(I, q, (uint32_t)I->start, m, st);
+    E[nE].id = (uint32_t)I->start;
+    E[nE++].d = ed[I->start];
+    const double d_start = ed[I->start];
+    int64_t b = P->beam;
+    const int64_t bmax = P->b_max > 0 ? P->b_max : b;
+    int first = 1;
+    for (;;) {
+        st->rounds++;
+        st->final_beam = (int32_t)b;
+        /* B <- the b closest points of E */
+        memcpy(B, E, (size_t)nE * sizeof(ent));
+        qsort(B, (size_t)nE, sizeof(ent), cmp_ent);
+        int64_t nb = nE < b ? nE : b;
+        for (int64_t i = 0; i < nb; i++) m->inB[B[i].id] = 1;
+        int stopped = 0;
+        int64_t round_visits = 0;
+        for (;;) {
+            int64_t ip = -1;
+            for (int64_t i = 0; i < nb; i++)
+                if (!m->inV[B[i].id]) { ip = i; break; }
+            if (ip < 0) break;
+            ent ps = B[ip];
+            if (use_es && B[0].d > r && round_visits >= P->es_vl &&
+                es_metric_exceeds(P->es_metric, ps.d, B, nb, P->es_radius, d_start)) {
+                stopped = 1;
+                break;
+            }
+            m->inV[ps.id] = 1;
+            nv++;
+            round_visits++;
+            const uint32_t *row = I->adj + (size_t)ps.id * I->R;
+            for (int k = 0; k < I->R; k++) {
+                uint32_t j = row[k];
+                if (j == OR_SENT || m->inV[j] || m->inB[j]) continue;
+                if (!m->inE[j]) {
+                    ed[j] = eval(I, q, j, m, st);
+                    E[nE].id = j;
+                    E[nE++].d = ed[j];
+                }
+                B[nb].id = j;
+                B[nb].d = ed[j];
+                m->inB[j] = 1;
+                nb++;
+            }
+            qsort(B, (size_t)nb, sizeof(ent), cmp_ent);
+            if (nb > b) {
+                for (int64_t i = b; i < nb; i++) m->inB[B[i].id] = 0;
+                nb = b;
+            }
+        }
+        if (first) st->early_stopped = stopped;
+        first = 0;
+        nres = 0;
+        for (int64_t i = 0; i < nb; i++) {
+            m->inB[B[i].id] = 0;
+            if (B[i].d <= r) res[nres++] = B[i];
+        }
+        if (nres < b) break;
+        st->phase = 2;
+        if (2 * b > bmax) { st->truncated = 1; break; }
+        b = 2 * b;
+    }
+    st->visits_beam = nv;
+    free(E); free(B); free(ed);
+    return nres;
+}
+
 int64_t or_range_search_one(const or_index *I, const void *q, double r, const or_params *P, uint32_t *ids,
                             double *dists, int64_t cap, or_stats *st) {
     memset(st, 0, sizeof(*st));
     marks m;
     if (!marks_init(&m, I->n)) { marks_free(&m); return -1; }
-    int use_es = (P->variant == OR_BEAM_ES || P->variant == OR_DOUBLING_ES || P->variant == OR_GREEDY_ES);
+    int use_es = (P->variant == OR_BEAM_ES || P->variant == OR_DOUBLING_ES || P->variant == OR_GREEDY_ES ||
+                  P->variant == OR_DOUBLING_WARM_ES);
+    if (P->variant == OR_DOUBLING_WARM || P->variant == OR_DOUBLING_WARM_ES) {
+        ent *wres = (ent *)malloc((size_t)I->n * sizeof(ent));
+        int64_t nw = wres ? warm_doubling(I, q, r, P, use_es, wres, &m, st) : -1;
+        for (int64_t i = 0; i < nw && i < cap; i++) {
+            ids[i] = wres[i].id;
+            dists[i] = wres[i].d;
+        }
+        free(wres);
+        marks_free(&m);
+        return nw;
+    }
     int doubling = (P->variant == OR_DOUBLING || P->variant == OR_DOUBLING_ES);
     int greedy = (P->variant == OR_GREEDY || P->variant == OR_GREEDY_ES);
     int64_t b = P->beam;

@@ -370,3 +370,58 @@ def test_multi_parent_invariants(small, small_runs, expand):
                 assert len(ids) <= 16
             if v == "greedy_es" and st["early_stopped"]:
                 assert len(ids) == 0
+
+
+# ---- warm-restart doubling (rounds continue instead of restarting; a variant of Alg. 3, not in the paper)
+
+def test_warm_doubling_equals_alg3_without_a_second_round(small, small_runs):
+    """The first round of both is Alg. 1 from the start point: if it ends with |N| < b there is no
+    second round, and the results agree."""
+    ds, idx = small
+    for v, w in (("doubling", "doubling_warm"), ("doubling_es", "doubling_warm_es")):
+        lit = small_runs[(v, 8)]
+        warm = oracle.range_search(idx, ds.Q, ds.radius, w, beam=8, b_max=4096)
+        single = 0
+        for x, y, sl, sw in zip(lit[0], warm[0], lit[2], warm[2]):
+            if sl["rounds"] == 1:
+                single += 1
+                assert np.array_equal(x, y) and sw["rounds"] == 1
+                assert sl["early_stopped"] == sw["early_stopped"]
+        assert single > 0
+
+
+@pytest.mark.parametrize("variant", ["doubling_warm", "doubling_warm_es"])
+def test_warm_doubling_invariants(small, variant):
+    """In range, unique, sorted, exact distances; no point visited twice; a stopped-early search is
+    empty; the final beam is b * 2^(rounds - 1) and ends below b unless truncated."""
+    ds, idx = small
+    ids_l, d_l, st_l = oracle.range_search(idx, ds.Q, ds.radius, variant, beam=8, b_max=4096)
+    for qi, (ids, d, st) in enumerate(zip(ids_l, d_l, st_l)):
+        eids, ed = _exact(ds, ds.Q[qi], ds.radius)
+        assert np.all(np.isin(ids, eids)) and len(np.unique(ids)) == len(ids)
+        assert np.array_equal(np.lexsort((ids, d)), np.arange(len(ids)))
+        ex = dict(zip(eids.tolist(), ed.tolist()))
+        assert all(ex[i] == dd for i, dd in zip(ids.tolist(), d.tolist()))
+        assert st["visits_beam"] <= ds.X.shape[0]
+        assert st["final_beam"] == 8 * 2 ** (st["rounds"] - 1)
+        assert st["truncated"] or len(ids) < st["final_beam"]
+        if st["early_stopped"]:
+            assert len(ids) == 0
+
+
+def test_warm_doubling_exhaustive_equals_brute_force(tiny):
+    ds, idx = tiny
+    n = ds.X.shape[0]
+    for qi in range(0, len(ds.Q), 3):
+        ids, d, st = oracle.range_search_one(idx, ds.Q[qi], ds.radius, "doubling_warm", beam=n + 1, b_max=4 * n)
+        eids, ed = _exact(ds, ds.Q[qi], ds.radius)
+        assert np.array_equal(ids, eids) and np.array_equal(d.astype(np.int64), ed)
+        assert st["visits_beam"] == n
+
+
+def test_warm_doubling_evaluates_each_point_once(small):
+    """Rounds never re-evaluate: the distance evaluations equal the distinct points evaluated."""
+    ds, idx = small
+    _, _, st_l = oracle.range_search(idx, ds.Q, ds.radius, "doubling_warm", beam=8, b_max=4096)
+    for st in st_l:
+        assert st["evals"] == st["distinct"]
