@@ -270,12 +270,6 @@ static int64_t greedy_search(const or_index *I, const void *q, const ent *S, int
     return nv;
 }
 
-/* ---------------------------------------------------------------- per-query driver
- * Alg. 6 for the greedy variants, Alg. 3 for the doubling variants, and the
- * plain beam-search baseline (return {n in B : d <= r}).  Results are written
- * sorted by (dist, id).  Returns the number of results, or -1 on allocation
- * failure.  If the count exceeds cap, nothing is written past cap and the
- * caller should retry with a larger buffer. */
 /* ---------------------------------------------------------------- warm-restart doubling
  * A variant of Alg. 3 that is not in the paper: instead of restarting every
  * round from B = S with V = {} (which re-visits and re-evaluates), a round
@@ -364,6 +358,12 @@ static int64_t warm_doubling(const or_index *I, const void *q, double r, const o
     return nres;
 }
 
+/* ---------------------------------------------------------------- per-query driver
+ * Alg. 6 for the greedy variants, Alg. 3 for the doubling variants, and the
+ * plain beam-search baseline (return {n in B : d <= r}).  Results are written
+ * sorted by (dist, id).  Returns the number of results, or -1 on allocation
+ * failure.  If the count exceeds cap, nothing is written past cap and the
+ * caller should retry with a larger buffer. */
 int64_t or_range_search_one(const or_index *I, const void *q, double r, const or_params *P, uint32_t *ids,
                             double *dists, int64_t cap, or_stats *st) {
     memset(st, 0, sizeof(*st));

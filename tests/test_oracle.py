@@ -1,14 +1,17 @@
 """Pins for the CPU oracle (no GPU).
 
 The oracle is checked against things other than itself:
-  * hand-worked traces of Alg. 1/2/3/5/6 (tests/golden/hand_traces.json);
+  * hand-worked traces of Alg. 1/2/3/5/6 (tests/golden/hand_traces.json) and of
+    Alg. 1 with the other early-stopping metrics of Sec. 3.2
+    (tests/golden/es_metric_traces.json);
   * Def. 2.1 brute force on tiny inputs where the search must be exhaustive
     (b >= n on a graph whose every node is reachable from the start point);
   * an independent reachability closure (scipy BFS) for Alg. 2;
   * invariants: results within r, no duplicates, sorted by (dist, id), subset
     of the exact set, |beam result| <= b, early stop returns the non-ES result
     or nothing, greedy extends the beam result;
-  * exact distances recomputed in numpy (int64 / fp64);
+  * exact distances recomputed in numpy (int64 / fp64) for every element type
+    and metric the oracle takes (uint8, int8, fp32; squared L2 and inner product);
   * Def. 2.2 on hand-computed values.
 """
 import json
@@ -59,6 +62,29 @@ def test_hand_traces(case):
         assert ds.tolist() == c["result_dist"]
 
 
+GOLD_ES = os.path.join(os.path.dirname(__file__), "golden", "es_metric_traces.json")
+
+
+@pytest.mark.parametrize("case", [c["name"] for c in json.load(open(GOLD_ES))["cases"]])
+def test_es_metric_hand_traces(case):
+    """Alg. 1 + Alg. 4 with M = d_top1, d_top10 or d_top10 / d_start on a star built so that
+    an off-by-one in the 10th-closest index, the farthest point in place of the 10th, or a
+    ratio against the wrong distance each changes when the search stops."""
+    g = json.load(open(GOLD_ES))
+    X = np.asarray(g["points"], np.uint8)[:, None]
+    adj = np.asarray([[SENT if v < 0 else v for v in row] for row in g["adjacency"]], np.uint32)
+    idx = oracle.Index(X, adj, g["start"])
+    c = [c for c in g["cases"] if c["name"] == case][0]
+    q = np.asarray([g["query"]], np.uint8)
+    B, Bd, V, stopped, st = oracle.beam_search(idx, q, [g["start"]], g["r"], c["b"], True, c["vl"], c["esr"],
+                                               es_metric=c["metric"])
+    assert B.tolist() == c["B"]
+    assert Bd.tolist() == [float((g["query"] - g["points"][i]) ** 2) for i in c["B"]]
+    assert V.tolist() == c["V"]
+    assert stopped == c["stopped"]
+    assert st["evals"] == c["evals"]
+
+
 # ------------------------------------------------------------------------------------------------
 # small synthetic datasets
 # ------------------------------------------------------------------------------------------------
@@ -107,6 +133,43 @@ def test_distances_exact_int64(tiny):
         got = oracle.distances(idx, ds.Q[qi], ids)
         diff = ds.X[ids].astype(np.int64) - ds.Q[qi].astype(np.int64)
         assert np.array_equal(got, (diff * diff).sum(1).astype(np.float64))
+
+
+@pytest.mark.parametrize("dtype,metric", [("u8", "ip"), ("i8", "l2"), ("i8", "ip"), ("f32", "l2"), ("f32", "ip")])
+def test_distances_every_branch(dtype, metric):
+    """Every element type and metric of the distance (Sec. 2: squared L2, negative inner
+    product), recomputed in numpy: int64 for 8-bit data (exact), fp64 for fp32 data."""
+    rng = np.random.default_rng(17)
+    n, d = 64, 37
+    if dtype == "u8":
+        X = rng.integers(0, 256, (n, d)).astype(np.uint8)
+    elif dtype == "i8":
+        X = rng.integers(-128, 128, (n, d)).astype(np.int8)
+    else:
+        X = rng.normal(size=(n, d)).astype(np.float32)
+    adj = np.full((n, 4), SENT, np.uint32)
+    idx = oracle.Index(X, adj, 0, metric=oracle.L2 if metric == "l2" else oracle.IP)
+    wide = np.float64 if dtype == "f32" else np.int64
+    for qi in range(5):
+        q = X[qi * 7 + 3]
+        ids = rng.integers(0, n, 40).astype(np.uint32)
+        got = oracle.distances(idx, q, ids)
+        x = X[ids].astype(wide)
+        qq = q.astype(wide)
+        want = ((x - qq) ** 2).sum(1) if metric == "l2" else -(x * qq).sum(1)
+        if dtype == "f32":
+            np.testing.assert_allclose(got, want, rtol=1e-12, atol=1e-12)
+        else:
+            assert np.array_equal(got, want.astype(np.float64))
+    # int8 extremes: |(-128) - 127|^2 * d and (-128)(-128) * d stay exact
+    if dtype == "i8":
+        lo = np.full(d, -128, np.int8)
+        hi = np.full(d, 127, np.int8)
+        X2 = np.stack([lo, hi])
+        i2 = oracle.Index(X2, np.full((2, 1), SENT, np.uint32), 0, metric=oracle.L2 if metric == "l2" else oracle.IP)
+        got = oracle.distances(i2, lo, np.array([0, 1], np.uint32))
+        want = [0.0, float(255 * 255 * d)] if metric == "l2" else [-float(128 * 128 * d), float(128 * 127 * d)]
+        assert got.tolist() == want
 
 
 def test_brute_force_matches_numpy(tiny):
