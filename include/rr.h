@@ -107,9 +107,8 @@ typedef struct {
  *                      |B| < 10) > esr
  *   RR_ES_TOP10_RATIO  d_top10 > t * d(start, q), t = es_radius (es_radius_mode
  *                      must be 1; squared L2 only)
- * Beam and greedy variants take every metric; the doubling variants take
- * RR_ES_VISITED only (RR_EINVAL otherwise); rr_beam_search_noalloc always uses
- * RR_ES_VISITED. */
+ * Beam and greedy variants take every metric (rr_beam_search_noalloc too);
+ * the doubling variants take RR_ES_VISITED only (RR_EINVAL otherwise). */
 typedef enum { RR_ES_VISITED = 0, RR_ES_TOP1 = 1, RR_ES_TOP10 = 2, RR_ES_TOP10_RATIO = 3 } rr_es_metric;
 
 /* Exact per-query counters (collect_stats = 1).  visits_* count |V| of the
@@ -179,6 +178,7 @@ typedef struct {
     int64_t device_bytes;  /* HBM held by the index (vectors, low-precision copies, adjacency) */
     int32_t row_stride;    /* bytes per stored vector (16-byte aligned) */
     int32_t device;
+    int64_t scratch_bytes; /* search scratch the index holds (device arenas + pinned staging); grow-only */
 } rr_index_info;
 
 rr_status rr_index_info_get(const rr_index *index, rr_index_info *info);
@@ -228,7 +228,12 @@ rr_status rr_last_profile(rr_index *index, rr_profile *out);
  * result and grows per-index scratch; this call allocates nothing.
  *   queries     nq x d device array of the index's element type
  *   radius      one radius for every query (metric units)
- *   variant     RR_BEAM or RR_BEAM_ES; params may be NULL (defaults; b <= 512)
+ *   variant     RR_BEAM or RR_BEAM_ES; params may be NULL (defaults; b <= 512).
+ *               The beam, the early-stop settings (every rr_es_metric) and the
+ *               launch shape (tile_hint, seen_log2, persistent) are honoured as
+ *               in rr_range_search; precision must be RR_PREC_EXACT (the
+ *               low-precision copies are allocated on first use): RR_EINVAL
+ *               otherwise
  *   out_counts  nq int32 (device): |N| of each query
  *   out_ids     nq x b uint32 (device): N of query i in out_ids[i*b ..], sorted
  *               by (distance, id); slots past out_counts[i] hold 0xFFFFFFFF
@@ -239,8 +244,9 @@ rr_status rr_last_profile(rr_index *index, rr_profile *out);
  * with RR_EINVAL -- split it.  The first call on a device looks the array's
  * address up (cudaGetSymbolAddress); make it before any stream capture.
  * Calls share the array: calls whose work overlaps on the GPU race, so
- * serialise them.  Returns after the stream has finished the call's work.
- * Results equal rr_range_search's for the same variant and beam. */
+ * serialise them.  The call synchronises `stream`: it returns after the stream
+ * has finished the call's work.  Results equal rr_range_search's for the same
+ * variant and params. */
 rr_status rr_beam_search_noalloc(rr_index *index, const void *queries, int64_t nq, double radius, int32_t variant,
                                  const rr_params *params, void *stream, int32_t *out_counts, uint32_t *out_ids,
                                  void *out_dists);
@@ -343,6 +349,19 @@ rr_status rr_result_free(rr_result *result);
 
 /* Message of the calling thread's last failure ("" if none). */
 const char *rr_last_error(void);
+
+/* Failure-path hooks for tests (the paper has no counterpart).  Process-wide,
+ * off by default; each takes effect for calls that start after it is set.
+ *   "fail_alloc_after"      value N >= 0: the library's (N+1)-th device
+ *                           scratch or result allocation from now on fails as
+ *                           if the device were out of memory (the call
+ *                           returns RR_ENOMEM and frees what it took); -1 = off
+ *   "beam_iteration_limit"  value L > 0: the beam and doubling kernels give up
+ *                           a query after L iterations of Alg. 1's loop and
+ *                           the call returns RR_EINTERNAL (the guard that
+ *                           normally sits at n + 1 iterations); 0 = default
+ * Returns RR_EINVAL for an unknown key. */
+rr_status rr_debug_set(const char *key, int64_t value);
 
 #ifdef __cplusplus
 }

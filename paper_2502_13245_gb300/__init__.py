@@ -35,7 +35,7 @@ EXPORTS = ["rr_params_init", "rr_create_index", "rr_load_index", "rr_free_index"
            "rr_range_search", "rr_brute_force", "rr_result_free", "rr_last_error", "rr_last_profile",
            "rr_beam_search_noalloc", "rr_serve_cfg_init", "rr_serve_create", "rr_serve_submit", "rr_serve_poll",
            "rr_serve_collect", "rr_serve_cancel", "rr_serve_stats", "rr_serve_destroy", "rr_result_to_host",
-           "rr_abi_sizes"]
+           "rr_abi_sizes", "rr_debug_set"]
 
 
 class RRError(RuntimeError):
@@ -99,7 +99,7 @@ class Result(ctypes.Structure):
 class IndexInfo(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("d", ctypes.c_int32), ("dtype", ctypes.c_int32), ("metric", ctypes.c_int32),
                 ("R", ctypes.c_int32), ("start", ctypes.c_int64), ("device_bytes", ctypes.c_int64),
-                ("row_stride", ctypes.c_int32), ("device", ctypes.c_int32)]
+                ("row_stride", ctypes.c_int32), ("device", ctypes.c_int32), ("scratch_bytes", ctypes.c_int64)]
 
 
 _lib = None
@@ -157,6 +157,8 @@ def load_library(path: str | None = None):
     L.rr_serve_stats.argtypes = [P, P, I32]
     L.rr_serve_destroy.restype = ctypes.c_int
     L.rr_serve_destroy.argtypes = [P]
+    L.rr_debug_set.restype = ctypes.c_int
+    L.rr_debug_set.argtypes = [ctypes.c_char_p, I64]
     _lib = L
     return L
 
@@ -294,15 +296,39 @@ def rr_beam_search_noalloc(handle, queries, radius, variant, params, out_counts,
     must already exist (out_counts: nq int32, out_ids: nq x b int32/uint32,
     out_dists: nq x b int32 or float32) and the library uses only a fixed static
     scratch array.  Returns the status (raises on errors other than RR_OK)."""
+    import torch
     qp, qdev, qk = _ptr_and_device(queries)
     nq = qk.shape[0]
     v = VARIANTS[variant] if isinstance(variant, str) else int(variant)
+    info = rr_index_info_get(handle)
+    beam = params.beam if params else rr_params_init().beam
+    dist_ok = (torch.float32,) if info.dtype == RR_F32 else (torch.int32,)
+    # the library cannot see the outputs' sizes: check them here, before anything is written
+    for name, t, numel, dts in (("out_counts", out_counts, nq, (torch.int32,)),
+                                ("out_ids", out_ids, nq * beam, (torch.int32, getattr(torch, "uint32", torch.int32))),
+                                ("out_dists", out_dists, nq * beam, dist_ok)):
+        if not isinstance(t, torch.Tensor) or not t.is_cuda:
+            raise ValueError("%s must be a CUDA tensor" % name)
+        if t.device.index != info.device:
+            raise ValueError("%s is on cuda:%d, the index on cuda:%d" % (name, t.device.index, info.device))
+        if not t.is_contiguous():
+            raise ValueError("%s must be contiguous" % name)
+        if t.numel() < numel:
+            raise ValueError("%s holds %d elements, the call writes %d" % (name, t.numel(), numel))
+        if t.dtype not in dts:
+            raise ValueError("%s has dtype %s, expected one of %s" % (name, t.dtype, dts))
     st = load_library().rr_beam_search_noalloc(handle, qp, nq, float(radius), v,
                                                ctypes.byref(params) if params else None,
                                                _stream_of(qdev, stream), out_counts.data_ptr(), out_ids.data_ptr(),
                                                out_dists.data_ptr())
     _check(st)
     return st
+
+
+def rr_debug_set(key: str, value: int):
+    """Failure-path hooks for tests: "fail_alloc_after" (N-th next device allocation fails; -1 off),
+    "beam_iteration_limit" (per-query iteration guard of the beam / doubling kernels; 0 default)."""
+    _check(load_library().rr_debug_set(key.encode(), int(value)))
 
 
 def rr_last_profile(handle) -> Profile:

@@ -168,7 +168,7 @@ __device__ __forceinline__ void search_query(const SearchArgs &a, int hlg, int64
             if (fire) { stopped = true; break; }
         }
         const uint32_t p = key_id(pk);
-        if (++guard > a.n + 1 || p >= (uint32_t)a.n) {  // cannot happen for a validated index
+        if (++guard > a.iter_limit || p >= (uint32_t)a.n) {  // cannot happen for a validated index
             if (lane == 0) atomicExch(a.error, p >= (uint32_t)a.n ? 3 : 1);
             break;
         }

@@ -165,7 +165,7 @@ __global__ void __launch_bounds__(128) round_kernel(DoublingRound d) {
             if (nI > 0 && (s.I[0] | 1ull) < mn) mn = s.I[0] | 1ull;
             if (key_dk(mn) > rks && nvis >= a.es_vl && key_dk(pk) > ek) { stopped = true; break; }
         }
-        if (++guard > a.n + 1) {
+        if (++guard > a.iter_limit) {
             if (lane == 0) atomicExch(a.error, 2);
             break;
         }

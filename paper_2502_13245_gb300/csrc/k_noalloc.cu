@@ -3,8 +3,8 @@
 //
 // Who needs this: code that runs where cudaMalloc is off limits -- inside a
 // host callback, on a thread that works under a fixed, pre-reserved memory
-// budget owned by someone else (an inference server's allocator, a graph
-// replay loop), or under a policy that forbids any allocation after start-up.
+// budget owned by someone else (an inference server's allocator), or under a
+// policy that forbids any allocation after start-up.
 // rr_range_search allocates its result arrays and grows per-index scratch, so
 // those callers cannot use it.  This entry point writes into output arrays the
 // caller already owns and keeps its intermediate data in one file-scope device
@@ -21,7 +21,14 @@
 // All calls share the array and it keeps the last call's contents, so every
 // call re-initialises what must start from zero.  Calls whose work overlaps
 // on the GPU (different streams, or different host threads) race on the array
-// and must be serialised by the caller.
+// and must be serialised by the caller.  Before returning, the call waits for
+// its stream to finish the work (it reads the device guard word back).
+//
+// Parameters are those of rr_range_search for RR_BEAM / RR_BEAM_ES: the beam,
+// the Alg. 5 / Alg. 4 early-stop settings (every metric), the launch shape
+// (tile_hint, seen_log2, persistent); results are equal for equal settings.
+// Low-precision traversal is refused (its traversal copies are allocated on
+// first use), as are per-query radii.
 #include <string.h>
 
 #include <algorithm>
@@ -112,6 +119,20 @@ extern "C" rr_status rr_beam_search_noalloc(rr_index *ix, const void *queries, i
     else rr_params_init(&P);
     if (P.beam < 1 || P.beam > 512) { set_error("rr_beam_search_noalloc: beam=%d out of [1, 512]", P.beam); return RR_EINVAL; }
     if (P.es_visit_limit < 0) { set_error("rr_beam_search_noalloc: es_visit_limit < 0"); return RR_EINVAL; }
+    if (P.es_metric < RR_ES_VISITED || P.es_metric > RR_ES_TOP10_RATIO) {
+        set_error("rr_beam_search_noalloc: unknown early-stopping metric %d", P.es_metric);
+        return RR_EINVAL;
+    }
+    if (variant == RR_BEAM_ES && P.es_metric == RR_ES_TOP10_RATIO && (P.es_radius_mode != 1 || ix->metric != RR_L2)) {
+        set_error("rr_beam_search_noalloc: the d_top10 / d_start metric takes its ratio from es_radius "
+                  "(es_radius_mode = 1) and needs squared L2");
+        return RR_EINVAL;
+    }
+    if (P.precision != RR_PREC_EXACT) {
+        // the BF16 / FP8 traversal copies are built (allocated) on first use
+        set_error("rr_beam_search_noalloc: only exact traversal (precision = RR_PREC_EXACT) allocates nothing");
+        return RR_EINVAL;
+    }
     DeviceGuard dg(ix->device);
     if (!is_device_ptr(queries) || !is_device_ptr(out_counts) || !is_device_ptr(out_ids) || !is_device_ptr(out_dists)) {
         set_error("rr_beam_search_noalloc: queries and outputs must be device memory");
@@ -174,6 +195,14 @@ extern "C" rr_status rr_beam_search_noalloc(rr_index *ix, const void *queries, i
     a.beam = b;
     a.use_es = variant == RR_BEAM_ES ? 1 : 0;
     a.es_vl = P.es_visit_limit;
+    a.es_metric = P.es_metric;
+    a.es_ratio = P.es_radius;
+    a.hash_lg = P.seen_log2;
+    a.persistent = P.persistent ? 1 : 0;
+    a.next_q = counters + 2;  // zeroed by init_kernel
+    a.d = ix->d;
+    a.prec = RR_PREC_EXACT;
+    a.iter_limit = beam_iteration_limit(ix->n);
     a.phase2 = 0;
     a.res_keys = (uint64_t *)(S + off_keys);
     a.res_count = (int32_t *)(S + off_cnt);

@@ -14,6 +14,10 @@ void set_error(const char *fmt, ...);
 void note_launch(int k = 1);
 int64_t launches_so_far();
 rr_status cuda_fail(cudaError_t e, const char *what);
+// failure-path hooks set by rr_debug_set: true if this device allocation is to fail;
+// the beam and doubling kernels' per-query iteration guard (default n + 1)
+bool inject_alloc_failure();
+int64_t beam_iteration_limit(int64_t n);
 
 #define RR_CUDA(call)                                        \
     do {                                                     \
@@ -136,6 +140,7 @@ struct SearchArgs {
     const float2 *lp_info;    // fp8: {scale, ||x||^2} per row
     float slackA, slackB, slackC;  // |d - d~| <= A ||q|| + B ||q||^2 + C
     float rel_eps;            // > 0: slack = rel_eps * |r| instead
+    int64_t iter_limit;       // per-query iteration guard of the beam / doubling kernels (n + 1 by default)
 };
 
 rr_status ensure_lowp(rr_index *ix, int prec, cudaStream_t st);

@@ -8,6 +8,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <string>
 #include <vector>
 
@@ -35,6 +36,23 @@ rr_status cuda_fail(cudaError_t e, const char *what) {
     return RR_ECUDA;
 }
 
+// Failure-path hooks (rr_debug_set): process-wide, off by default.
+static std::atomic<int64_t> g_fail_alloc_after{-1};
+static std::atomic<int64_t> g_beam_iteration_limit{0};
+
+bool inject_alloc_failure() {
+    int64_t v = g_fail_alloc_after.load();
+    while (v >= 0) {
+        if (g_fail_alloc_after.compare_exchange_weak(v, v - 1)) return v == 0;
+    }
+    return false;
+}
+
+int64_t beam_iteration_limit(int64_t n) {
+    const int64_t v = g_beam_iteration_limit.load();
+    return v > 0 ? v : n + 1;
+}
+
 rr_status Arena::reserve(size_t bytes) {
     if (bytes <= cap) return RR_OK;
     if (base) {
@@ -44,7 +62,7 @@ rr_status Arena::reserve(size_t bytes) {
         if (e != cudaSuccess) return cuda_fail(e, "cudaFree(arena)");
     }
     size_t want = std::max(bytes, (size_t)1 << 24);
-    cudaError_t e = cudaMalloc(&base, want);
+    cudaError_t e = inject_alloc_failure() ? cudaErrorMemoryAllocation : cudaMalloc(&base, want);
     if (e != cudaSuccess) {
         cudaGetLastError();
         base = nullptr;
@@ -95,7 +113,7 @@ rr_status grow(Grow &g, size_t need, size_t keep, cudaStream_t st) {
     if (need <= g.bytes) return RR_OK;
     size_t want = std::max(need, g.bytes + g.bytes / 2);
     void *np = nullptr;
-    cudaError_t e = cudaMalloc(&np, want);
+    cudaError_t e = inject_alloc_failure() ? cudaErrorMemoryAllocation : cudaMalloc(&np, want);
     if (e != cudaSuccess) {
         cudaGetLastError();
         set_error("device allocation of %zu bytes failed: %s", want, cudaGetErrorString(e));
@@ -297,7 +315,24 @@ rr_status rr_index_info_get(const rr_index *ix, rr_index_info *info) {
     info->n = ix->n; info->d = ix->d; info->dtype = ix->dtype; info->metric = ix->metric; info->R = ix->R;
     info->start = ix->start; info->device_bytes = ix->device_bytes; info->row_stride = ix->row_stride;
     info->device = ix->device;
+    info->scratch_bytes = (int64_t)ix->arena.cap + (int64_t)ix->phase2.bytes + (int64_t)ix->item_key.bytes +
+                          (int64_t)ix->item_slot.bytes + (int64_t)ix->outbuf.bytes + (int64_t)ix->dbl_s[0].bytes +
+                          (int64_t)ix->dbl_s[1].bytes + (int64_t)ix->dbl_tmp.bytes + (int64_t)ix->pinned.cap;
     return RR_OK;
+}
+
+rr_status rr_debug_set(const char *key, int64_t value) {
+    if (!key) { set_error("rr_debug_set: key is NULL"); return RR_EINVAL; }
+    if (!strcmp(key, "fail_alloc_after")) {
+        g_fail_alloc_after.store(value < 0 ? -1 : value);
+        return RR_OK;
+    }
+    if (!strcmp(key, "beam_iteration_limit")) {
+        g_beam_iteration_limit.store(value < 0 ? 0 : value);
+        return RR_OK;
+    }
+    set_error("rr_debug_set: unknown key '%s'", key);
+    return RR_EINVAL;
 }
 
 void rr_abi_sizes(int64_t out[7]) {

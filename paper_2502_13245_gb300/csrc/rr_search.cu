@@ -36,7 +36,7 @@ struct Search {
 
     void *res_alloc(size_t bytes) {
         void *p = nullptr;
-        if (cudaMallocAsync(&p, std::max<size_t>(bytes, 8), st) != cudaSuccess) {
+        if (inject_alloc_failure() || cudaMallocAsync(&p, std::max<size_t>(bytes, 8), st) != cudaSuccess) {
             cudaGetLastError();
             return nullptr;
         }
@@ -503,6 +503,7 @@ extern "C" rr_status rr_range_search(rr_index *ix, const void *queries, int64_t 
     a.hash_lg = P.seen_log2;
     a.persistent = P.persistent ? 1 : 0;
     a.next_q = a.p2_count + 2;  // zeroed with the other counters in stage()
+    a.iter_limit = beam_iteration_limit(ix->n);
     a.d = ix->d;
     a.prec = RR_PREC_EXACT;
     if (P.precision != RR_PREC_EXACT) {

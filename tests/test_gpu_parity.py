@@ -264,3 +264,27 @@ def test_rrx_file_roundtrip(rr, c0, c0_oracle, tmp_path):
     assert gi.info.n == c0.X.shape[0] and gi.info.R == c0.adj.shape[1] and gi.info.start == c0.start
     o_ids, o_d, _ = oracle_run(c0_oracle, c0, "greedy_es", 32)
     assert_same(gi.range_search(c0.Q, c0.radius, "greedy_es", beam=32), o_ids, o_d, len(c0.Q))
+
+
+@pytest.mark.parametrize("variant,beam", [("greedy", 32), ("doubling_es", 16), ("beam_es", 64)])
+def test_profiled_calls_are_bit_exact(rr, c0, c0_index, c0_oracle, variant, beam):
+    """profile = 1 records CUDA events between the phases and counts launches; the results are
+    those of the unprofiled call (device queries, device results, the tuned launch shape)."""
+    import torch
+    Qd = torch.from_numpy(c0.Q).cuda()
+    o_ids, o_d, _ = oracle_run(c0_oracle, c0, variant, beam)
+    for prof in (1, 0):
+        p = rr.rr_params_init(beam=beam, profile=prof, persistent=1, tile_hint=4, seen_log2=10)
+        st, res = rr.rr_range_search(c0_index.h, Qd, c0.radius, variant, p, result_on_device=True)
+        assert st == rr.RR_OK
+        pr = rr.rr_last_profile(c0_index.h)
+        h = rr.rr_result_to_host(res)
+        rr.rr_result_free(res)
+        assert_same(rr.RangeResult(h), o_ids, o_d, len(c0.Q))
+        if prof:
+            assert pr.valid == 1 and pr.launches >= 2
+            assert pr.beam_ms > 0 and pr.total_ms >= pr.beam_ms
+            if variant == "beam_es":
+                assert pr.phase2_queries == 0 and pr.phase2_steps == 0
+        else:
+            assert pr.valid == 0
