@@ -41,7 +41,8 @@ typedef enum {
     RR_ENOMEM = 2,     /* host or device allocation failed */
     RR_ECUDA = 3,      /* a CUDA runtime call failed */
     RR_EFORMAT = 4,    /* index file malformed or checksum mismatch */
-    RR_EOVERFLOW = 5,  /* results exceeded max_results_total (result kept, flags set) */
+    RR_EOVERFLOW = 5,  /* phase-2 results exceeded max_results_total, or doubling hit b_max
+                          (a valid, truncated result is kept; RR_FLAG_TRUNCATED marks the queries) */
     RR_ETIMEOUT = 6,   /* a device wait or host poll ran out of time */
     RR_EBUSY = 7,      /* serving: request not finished yet, or queue full */
     RR_EINTERNAL = 8   /* a device-side guard tripped (should not happen) */
@@ -90,7 +91,8 @@ typedef struct {
     float recheck_eps;         /* low-precision slack: recheck when approx <= r + eps*|r| (0 = derive) */
     int32_t persistent;        /* 1: one persistent launch with a device work queue */
     int32_t collect_stats;     /* 1: fill rr_result.stats (exact visit / distinct-id counts) */
-    int64_t max_results_total; /* cap on the summed result count (0 = default 1<<28) */
+    int64_t max_results_total; /* cap on the summed results of the greedy / doubling phase (0 = default
+                                  1<<28); each query's first beam (at most b results) is always kept */
     int32_t tile_hint;         /* warps per CTA for the beam kernel (0 = library choice) */
     int32_t profile;           /* 1: record per-phase device times, see rr_last_profile */
     int32_t seen_log2;         /* log2 slots of the beam kernel's seen table, 5..14 (0 = library choice) */
@@ -156,6 +158,42 @@ void rr_params_init(rr_params *p);
 rr_status rr_create_index(const void *vectors, int64_t n, int32_t d, int32_t dtype, int32_t metric,
                           const uint32_t *adjacency, int32_t R, int64_t start, int32_t device,
                           int32_t validate, rr_index **out);
+
+/* Build a proximity graph on the GPU: a deterministic Vamana-style graph (the
+ * paper searches a DiskANN / Vamana graph with parameters R, L and alpha,
+ * Sec. 4.1, and leaves its construction to that system; this is the
+ * construction step of the index, not the range search).
+ *   vectors    n x d row-major uint8 or int8 (dtype), host or device memory
+ *   metric     RR_L2 or RR_IP (alpha applies to the metric value: squared L2)
+ *   R, L       out-degree bound (2..128) and construction beam (1..512)
+ *   alpha      RobustPrune's alpha (>= 1); with passes >= 2 the first pass
+ *              uses alpha = 1
+ *   seed       insertion order (a seeded permutation with `start` first)
+ *   start      the entry point (the medoid); every point ends up reachable
+ *              from it (a final repair attaches unreached points)
+ *   adjacency  out: n x R uint32 in HOST memory, 0xFFFFFFFF pads each row
+ *   info       optional: batches run, points attached by the repair, time
+ * Batches of 1, 2, 4, ... points (capped at n/50) each search the graph as it
+ * stood before the batch (Alg. 1 with beam L from start), RobustPrune their
+ * first 4L + 16 visits plus their current neighbours into a row of at most
+ * R - max(1, R/16) entries, then merge reverse edges per target in batch
+ * order (appended, or the target re-pruned when its row would overflow).
+ * Every order is by (distance, id) and every step reads a snapshot, so the
+ * result does not depend on the GPU's scheduling: for the same arguments it
+ * equals the project's CPU builder (rrsynth) array for array.  Device memory:
+ * about n*(row + 4R + 12) bytes plus n/50 * (8*(4L+16) + 28R) bytes of batch
+ * scratch.  fp32 vectors: RR_EINVAL.  Errors: RR_EINVAL, RR_ENOMEM, RR_ECUDA,
+ * RR_EINTERNAL (a device guard). */
+typedef struct {
+    int64_t batches;        /* insertion batches over all passes */
+    int64_t repaired;       /* points attached by the reachability repair */
+    double gpu_seconds;     /* wall time of the passes (device work + copies) */
+    double repair_seconds;  /* wall time of the host-side repair */
+} rr_build_info;
+
+rr_status rr_build_graph(const void *vectors, int64_t n, int32_t d, int32_t dtype, int32_t metric, int32_t R,
+                         int32_t L, double alpha, int32_t passes, uint64_t seed, int64_t start, int32_t device,
+                         uint32_t *adjacency, rr_build_info *info);
 
 /* Load an index file (.rrx, little endian): a 64-byte header
  *   'RRX1', u32 version 1, i64 n, i32 d, i32 dtype, i32 metric, i32 R,
@@ -340,9 +378,9 @@ rr_status rr_serve_destroy(rr_server *srv);
 rr_status rr_result_to_host(const rr_result *result, rr_result *host);
 
 /* sizeof of the public structs, for bindings to check their layouts against:
- * out[0..6] = rr_params, rr_query_stats, rr_result, rr_index_info, rr_profile,
- * rr_serve_cfg, rr_serve_stats_t.  Needs no GPU. */
-void rr_abi_sizes(int64_t out[7]);
+ * out[0..7] = rr_params, rr_query_stats, rr_result, rr_index_info, rr_profile,
+ * rr_serve_cfg, rr_serve_stats_t, rr_build_info.  Needs no GPU. */
+void rr_abi_sizes(int64_t out[8]);
 
 /* Free the arrays of a result (host or device) and zero the struct. */
 rr_status rr_result_free(rr_result *result);

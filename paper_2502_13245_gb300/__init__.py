@@ -35,7 +35,7 @@ EXPORTS = ["rr_params_init", "rr_create_index", "rr_load_index", "rr_free_index"
            "rr_range_search", "rr_brute_force", "rr_result_free", "rr_last_error", "rr_last_profile",
            "rr_beam_search_noalloc", "rr_serve_cfg_init", "rr_serve_create", "rr_serve_submit", "rr_serve_poll",
            "rr_serve_collect", "rr_serve_cancel", "rr_serve_stats", "rr_serve_destroy", "rr_result_to_host",
-           "rr_abi_sizes", "rr_debug_set"]
+           "rr_abi_sizes", "rr_debug_set", "rr_build_graph"]
 
 
 class RRError(RuntimeError):
@@ -102,6 +102,14 @@ class IndexInfo(ctypes.Structure):
                 ("row_stride", ctypes.c_int32), ("device", ctypes.c_int32), ("scratch_bytes", ctypes.c_int64)]
 
 
+class BuildInfo(ctypes.Structure):
+    _fields_ = [("batches", ctypes.c_int64), ("repaired", ctypes.c_int64), ("gpu_seconds", ctypes.c_double),
+                ("repair_seconds", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 _lib = None
 
 
@@ -159,6 +167,8 @@ def load_library(path: str | None = None):
     L.rr_serve_destroy.argtypes = [P]
     L.rr_debug_set.restype = ctypes.c_int
     L.rr_debug_set.argtypes = [ctypes.c_char_p, I64]
+    L.rr_build_graph.restype = ctypes.c_int
+    L.rr_build_graph.argtypes = [P, I64, I32, I32, I32, I32, I32, D, I32, ctypes.c_uint64, I64, I32, P, P]
     _lib = L
     return L
 
@@ -174,10 +184,10 @@ def _check(status):
 
 def rr_abi_sizes() -> dict:
     """sizeof of the public C structs as the library was compiled (layout check for this binding)."""
-    out = (ctypes.c_int64 * 7)()
+    out = (ctypes.c_int64 * 8)()
     load_library().rr_abi_sizes(out)
     names = ["rr_params", "rr_query_stats", "rr_result", "rr_index_info", "rr_profile", "rr_serve_cfg",
-             "rr_serve_stats_t"]
+             "rr_serve_stats_t", "rr_build_info"]
     return dict(zip(names, list(out)))
 
 
@@ -229,6 +239,17 @@ def rr_create_index(vectors, adjacency, start, metric=RR_L2, device=0, validate=
     _check(load_library().rr_create_index(vp, n, d, _dtype_code(vk), metric, ap, R, int(start), device,
                                           1 if validate else 0, ctypes.byref(h)))
     return h
+
+
+def rr_build_graph(vectors, R, L, alpha, passes=2, seed=0, start=0, metric=RR_L2, device=0):
+    """Proximity graph on the GPU (8-bit vectors, host or device): returns (adjacency uint32 [n, R], info dict)."""
+    vp, _, vk = _ptr_and_device(vectors)
+    n, d = vk.shape
+    adj = np.empty((n, R), dtype=np.uint32)
+    info = BuildInfo()
+    _check(load_library().rr_build_graph(vp, n, d, _dtype_code(vk), metric, R, L, float(alpha), passes, int(seed),
+                                         int(start), device, adj.ctypes.data, ctypes.byref(info)))
+    return adj, info.as_dict()
 
 
 def rr_load_index(path: str, device=0):

@@ -63,7 +63,7 @@ __device__ __forceinline__ int next_unvisited(const uint64_t *B, int n, int from
     return n;
 }
 
-template <int DT, int CPL, int BMAX, bool COUNT>
+template <int DT, int CPL, int BMAX, bool COUNT, bool BUILD>
 __device__ __forceinline__ void search_query(const SearchArgs &a, int hlg, int64_t qi, uint8_t *base);
 
 // 8-bit searches fit 64 registers with a few bytes of spill and gain from the extra resident
@@ -75,7 +75,7 @@ constexpr int kBeamMinBlocks = (DT == DT_U8 || DT == DT_I8) ? 4 : 3;
 // persistent = 1: a grid sized to the resident capacity; every warp takes the
 // next query from a device counter until the batch is done, so warps freed by
 // cheap (e.g. early-stopped) queries move on to the rest of the batch.
-template <int DT, int CPL, int BMAX, bool COUNT>
+template <int DT, int CPL, int BMAX, bool COUNT, bool BUILD = false>
 __global__ void __launch_bounds__(256, kBeamMinBlocks<DT>) beam_kernel(SearchArgs a, int hlg, int persistent, int32_t *next_q) {
     extern __shared__ __align__(16) uint8_t smem_raw[];
     const int lane = lane_id();
@@ -87,7 +87,7 @@ __global__ void __launch_bounds__(256, kBeamMinBlocks<DT>) beam_kernel(SearchArg
     qi = __shfl_sync(0xffffffffu, qi, 0);
     // whole warps leave together; the kernel has no block barriers
     while (qi < a.nq) {
-        search_query<DT, CPL, BMAX, COUNT>(a, hlg, qi, base);
+        search_query<DT, CPL, BMAX, COUNT, BUILD>(a, hlg, qi, base);
         if (!persistent) break;
         __syncwarp();
         if (lane == 0) qi = atomicAdd(next_q, 1);
@@ -95,7 +95,7 @@ __global__ void __launch_bounds__(256, kBeamMinBlocks<DT>) beam_kernel(SearchArg
     }
 }
 
-template <int DT, int CPL, int BMAX, bool COUNT>
+template <int DT, int CPL, int BMAX, bool COUNT, bool BUILD>
 __device__ __forceinline__ void search_query(const SearchArgs &a, int hlg, int64_t qi, uint8_t *base) {
     constexpr int UN = CPL == 1 ? 8 : (CPL == 2 ? 4 : 2);
     const int lane = lane_id();
@@ -118,11 +118,13 @@ __device__ __forceinline__ void search_query(const SearchArgs &a, int hlg, int64
     if constexpr (LP) {
         load_query_lp<DT>(a, reinterpret_cast<const float *>(a.queries + (size_t)qi * a.row_stride), qf);
         qn2 = query_norm2_lp(a, qf);
+    } else if constexpr (BUILD) {
+        load_query<CPL>(a, a.vec + (size_t)a.qids[qi] * a.row_stride, q);
     } else {
         load_query<CPL>(a, a.queries + (size_t)qi * a.row_stride, q);
     }
-    const uint32_t rk = a.rkey[qi];
-    const uint32_t ek = a.eskey[qi];
+    const uint32_t rk = BUILD ? 0u : a.rkey[qi];
+    const uint32_t ek = BUILD ? 0u : a.eskey[qi];
     // low precision: approximate distances above r + slack are certainly out of range
     const uint32_t rks = LP ? slack_key(a, rk, qn2) : rk;
     uint32_t *cbits = COUNT ? a.count_bits + (size_t)qi * a.words_per_q : nullptr;
@@ -152,7 +154,7 @@ __device__ __forceinline__ void search_query(const SearchArgs &a, int hlg, int64
         // p* <- argmin over B \ V = B[cur] (B sorted, everything before cur visited)
         const uint64_t pk = B[cur];
         // Alg. 5 / Alg. 4: closest of B outside r, |V| >= vl, the metric above its threshold
-        if (a.use_es && key_dk(B[0]) > rks && nvis >= a.es_vl) {
+        if (!BUILD && a.use_es && key_dk(B[0]) > rks && nvis >= a.es_vl) {
             bool fire;
             const uint32_t d10 = key_dk(B[min(nb, 10) - 1]);
             switch (a.es_metric) {
@@ -173,7 +175,10 @@ __device__ __forceinline__ void search_query(const SearchArgs &a, int hlg, int64
             break;
         }
         __syncwarp();
-        if (lane == 0) B[cur] = pk | 1ull;  // V <- V u {p*}
+        if (lane == 0) {
+            B[cur] = pk | 1ull;  // V <- V u {p*}
+            if (BUILD && nvis < a.vis_cap) a.vis_out[(size_t)qi * a.vis_cap + nvis] = pk & ~1ull;
+        }
         nvis++;
         __syncwarp();
         const int nxt = next_unvisited(B, nb, cur + 1);
@@ -288,6 +293,10 @@ __device__ __forceinline__ void search_query(const SearchArgs &a, int hlg, int64
         cur = min(min(posn, lb0), nb);
     }
 
+    if constexpr (BUILD) {
+        if (lane == 0) a.vis_count[qi] = min(nvis, a.vis_cap);
+        return;
+    }
     // N = {n in B : d(n, q) <= r}: a prefix of the sorted beam.  Low precision: the
     // prefix within r + slack is re-checked in exact fp32 and re-sorted by exact keys.
     int cnt = 0;
@@ -367,9 +376,47 @@ rr_status launch_b(const SearchArgs &a, int wpc, int hlg, cudaStream_t st) {
     return RR_EINVAL;
 }
 
+template <int DT, int BMAX>
+rr_status launch_build_k(const SearchArgs &a, int wpc, int hlg, cudaStream_t st) {
+    auto k = beam_kernel<DT, 1, BMAX, false, true>;
+    const size_t smem = (size_t)wpc * warp_smem_bytes(BMAX, a.R, hlg);
+    RR_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int64_t blocks = (a.nq + wpc - 1) / wpc;
+    k<<<(unsigned)blocks, 32 * wpc, smem, st>>>(a, hlg, 0, nullptr);
+    RR_CUDA(cudaGetLastError());
+    note_launch();
+    return RR_OK;
+}
+
+template <int DT>
+rr_status launch_build_b(const SearchArgs &a, int wpc, int hlg, cudaStream_t st) {
+    if (a.beam <= 32) return launch_build_k<DT, 32>(a, wpc, hlg, st);
+    if (a.beam <= 64) return launch_build_k<DT, 64>(a, wpc, hlg, st);
+    if (a.beam <= 128) return launch_build_k<DT, 128>(a, wpc, hlg, st);
+    if (a.beam <= 256) return launch_build_k<DT, 256>(a, wpc, hlg, st);
+    if (a.beam <= 512) return launch_build_k<DT, 512>(a, wpc, hlg, st);
+    set_error("graph build: L=%d exceeds the shared-memory beam limit 512", a.beam);
+    return RR_EINVAL;
+}
+
 }  // namespace
 
 int beam_hash_lg(int beam) { return beam <= 256 ? 10 : 11; }
+
+rr_status launch_build_search(const SearchArgs &a, int wpc, cudaStream_t st, int dtype_code) {
+    if (a.nq == 0) return RR_OK;
+    if (!a.qids || !a.vis_out || !a.vis_count || a.vis_cap < 1 || a.row_chunks > 32) {
+        set_error("graph build: bad search arguments");
+        return RR_EINTERNAL;
+    }
+    const int hlg = a.hash_lg > 0 ? a.hash_lg : beam_hash_lg(a.beam);
+    switch (dtype_code) {
+        case DT_U8: return launch_build_b<DT_U8>(a, wpc, hlg, st);
+        case DT_I8: return launch_build_b<DT_I8>(a, wpc, hlg, st);
+    }
+    set_error("graph build: the GPU builder takes 8-bit vectors");
+    return RR_EINVAL;
+}
 
 rr_status launch_beam(const SearchArgs &a, int wpc, cudaStream_t st, int dtype_code) {
     if (a.nq == 0) return RR_OK;

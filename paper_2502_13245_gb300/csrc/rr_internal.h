@@ -141,12 +141,23 @@ struct SearchArgs {
     float slackA, slackB, slackC;  // |d - d~| <= A ||q|| + B ||q||^2 + C
     float rel_eps;            // > 0: slack = rel_eps * |r| instead
     int64_t iter_limit;       // per-query iteration guard of the beam / doubling kernels (n + 1 by default)
+    // graph construction (launch_build_search): query i is the stored row qids[i]; the first vis_cap
+    // visits of query i are written, in visit order, to vis_out[i * vis_cap ..] and their number to
+    // vis_count[i]
+    const uint32_t *qids;
+    uint32_t *adj_w;          // the adjacency, writable (construction only)
+    uint64_t *vis_out;
+    int32_t vis_cap;
+    int32_t *vis_count;
 };
 
 rr_status ensure_lowp(rr_index *ix, int prec, cudaStream_t st);
 void slack_coefficients(const rr_index *ix, int prec, float *A, float *Bq, float *C);
 
 rr_status launch_beam(const SearchArgs &a, int warps_per_cta, cudaStream_t s, int dtype_code);
+// Alg. 1 without early stop or range filter for graph construction: the queries are stored rows
+// (a.qids), the visits are recorded (a.vis_out); 8-bit indexes only
+rr_status launch_build_search(const SearchArgs &a, int warps_per_cta, cudaStream_t s, int dtype_code);
 int beam_hash_lg(int beam);
 
 struct GreedyArgs {

@@ -335,8 +335,9 @@ rr_status rr_debug_set(const char *key, int64_t value) {
     return RR_EINVAL;
 }
 
-void rr_abi_sizes(int64_t out[7]) {
+void rr_abi_sizes(int64_t out[8]) {
     if (!out) return;
+    out[7] = sizeof(rr_build_info);
     out[0] = sizeof(rr_params);
     out[1] = sizeof(rr_query_stats);
     out[2] = sizeof(rr_result);

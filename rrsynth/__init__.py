@@ -74,12 +74,24 @@ def start_point(X: np.ndarray) -> int:
 
 
 def build_graph(X: np.ndarray, R: int, L: int, alpha: float, metric: int = M_L2, passes: int = 2,
-                seed: int = 0, threads: int = 0, start: int | None = None):
-    """Deterministic Vamana-style graph: returns (adj uint32 [n,R], start id)."""
+                seed: int = 0, threads: int = 0, start: int | None = None, builder: str = "cpu"):
+    """Deterministic Vamana-style graph: returns (adj uint32 [n,R], start id).
+
+    builder "cpu": vamana.c on the host cores.  builder "gpu": the same
+    procedure run by the CUDA library's rr_build_graph (8-bit data only), which
+    gives the same adjacency array (tested on C0, C1 and a d=256 sample of the
+    C3 recipe); it is used where the host build would take the better part of
+    an hour (C3)."""
     X = np.ascontiguousarray(X)
     n, d = X.shape
     if start is None:
         start = start_point(X)
+    if builder == "gpu":
+        import paper_2502_13245_gb300 as rr
+        rr.build()
+        adj, _ = rr.rr_build_graph(X, R, L, alpha, passes=passes, seed=seed, start=start,
+                                   metric=rr.RR_IP if metric == M_IP else rr.RR_L2)
+        return adj, int(start)
     adj = np.empty((n, R), dtype=np.uint32)
     rc = _load().rrs_build_vamana(X.ctypes.data, n, d, _dtype_code(X), metric, R, L, float(alpha), passes,
                                   seed, threads, adj.ctypes.data, start)
@@ -300,6 +312,7 @@ class Config:
     near_sigma: float
     zero_frac: float = 0.6
     streams: int = 0           # > 0: base rows drawn from that many seeded streams in parallel
+    builder: str = "cpu"       # graph builder: "cpu" (vamana.c) or "gpu" (the same procedure in librr)
 
 
 CONFIGS = {
@@ -309,10 +322,10 @@ CONFIGS = {
     "c1": Config("c1", 1_000_000, 128, 10_000, "u8", M_L2, 1000, 12.0, 5000, 64, 128, 1.2, 2, 1, 2.0),
     # 1,000,000 x 200 fp32 unit vectors, inner product, 10,000 queries, R=64 L=128 alpha=1.0
     "c2": Config("c2", 1_000_000, 200, 10_000, "f32", M_IP, 1000, 0.06, 5000, 64, 128, 1.0, 1, 2, 0.01),
-    # 10,000,000 x 256 uint8, 5,000 centres, families up to 20,000, 100,000 queries, R=64 L=48 alpha=1.2,
-    # one construction pass (minutes on the host's cores instead of the better part of an hour for two)
-    "c3": Config("c3", 10_000_000, 256, 100_000, "u8", M_L2, 5000, 12.0, 20000, 64, 48, 1.2, 1, 3, 2.0,
-                 streams=64),
+    # 10,000,000 x 256 uint8, 5,000 centres, families up to 20,000, 100,000 queries, R=64 L=128 alpha=1.2,
+    # two construction passes, built on the GPU (the host build of this graph takes the better part of an hour)
+    "c3": Config("c3", 10_000_000, 256, 100_000, "u8", M_L2, 5000, 12.0, 20000, 64, 128, 1.2, 2, 3, 2.0,
+                 streams=64, builder="gpu"),
 }
 
 
@@ -374,7 +387,8 @@ def make_dataset(cfg: Config, cache_dir: str | None = None, threads: int = 0, ve
     radius = pick_radius(nn1, cfg.zero_frac)
     radius = int(radius) if cfg.dtype == "u8" else float(radius)
     t2 = time.time()
-    adj, start = build_graph(X, cfg.R, cfg.L_build, cfg.alpha, cfg.metric, cfg.passes, cfg.seed, threads)
+    adj, start = build_graph(X, cfg.R, cfg.L_build, cfg.alpha, cfg.metric, cfg.passes, cfg.seed, threads,
+                             builder=cfg.builder)
     t3 = time.time()
     if verbose:
         print("[rrsynth] %s: gen %.1fs radius %.1fs graph %.1fs" % (cfg.name, t1 - t0, t2 - t1, t3 - t2),

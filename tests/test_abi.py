@@ -77,7 +77,25 @@ def test_binding_struct_layouts_match_the_library():
     sizes = rr.rr_abi_sizes()
     mirror = {"rr_params": rr.Params, "rr_query_stats": rr.QueryStats, "rr_result": rr.Result,
               "rr_index_info": rr.IndexInfo, "rr_profile": rr.Profile, "rr_serve_cfg": rr.ServeCfg,
-              "rr_serve_stats_t": rr.ServeStats}
+              "rr_serve_stats_t": rr.ServeStats, "rr_build_info": rr.BuildInfo}
     for name, cls in mirror.items():
         assert ctypes.sizeof(cls) == sizes[name], (name, ctypes.sizeof(cls), sizes[name])
     assert rr.STATS_DTYPE.itemsize == sizes["rr_query_stats"]
+
+
+def test_graph_builder_arguments_are_checked_without_gpu():
+    import numpy as np
+    import paper_2502_13245_gb300 as rr
+    L = rr.load_library()
+    X = np.zeros((10, 4), np.float32)
+    adj = np.zeros((10, 4), np.uint32)
+    assert L.rr_build_graph(X.ctypes.data, 10, 4, rr.RR_F32, rr.RR_L2, 4, 8, 1.2, 2, 0, 0, 0, adj.ctypes.data,
+                            None) == rr.RR_EINVAL
+    assert "8-bit" in rr.rr_last_error()
+    Xu = np.zeros((10, 4), np.uint8)
+    assert L.rr_build_graph(Xu.ctypes.data, 10, 4, rr.RR_U8, rr.RR_L2, 4, 8, 0.5, 2, 0, 0, 0, adj.ctypes.data,
+                            None) == rr.RR_EINVAL
+    assert L.rr_build_graph(Xu.ctypes.data, 10, 4, rr.RR_U8, rr.RR_L2, 4, 8, 1.2, 2, 0, 10, 0, adj.ctypes.data,
+                            None) == rr.RR_EINVAL
+    assert L.rr_build_graph(None, 10, 4, rr.RR_U8, rr.RR_L2, 4, 8, 1.2, 2, 0, 0, 0, adj.ctypes.data,
+                            None) == rr.RR_EINVAL

@@ -57,7 +57,10 @@ def test_overflow_keeps_a_truncated_subset(env):
     assert res.status == rr.RR_EOVERFLOW
     trunc = (res.flags & rr.RR_FLAG_TRUNCATED) != 0
     assert trunc.any()
-    assert len(res.ids) <= max(cap, heavy * beam)
+    # the cap bounds the greedy phase's results; every query keeps its first beam
+    p2 = (res.flags & rr.RR_FLAG_PHASE2) != 0
+    assert p2.sum() == heavy
+    assert int(np.diff(res.offsets)[p2].sum()) <= max(cap, heavy * beam)
     for i in range(len(ds.Q)):
         ids, d = res.query(i)
         if trunc[i]:
