@@ -1,9 +1,10 @@
 """Benchmark: batched range retrieval on a proximity graph, one GB300 per rank.
 
-Workload (default): 1,000,000 uint8 vectors, d=128, 1,000-centre Gaussian
-mixture with near-duplicate families; Vamana-style graph R=64, L_build=128,
-alpha=1.2 (built once, deterministic, not timed); 10,000 queries; squared-L2
-radius chosen so that ~60% of the queries match nothing.
+Workload (default): 10,000,000 uint8 vectors, d=256, 5,000-centre Gaussian
+mixture with near-duplicate families (up to 20,000 points); Vamana-style graph
+R=64, L_build=128, alpha=1.2, two passes (built once on the GPU,
+deterministic, not timed); 100,000 queries; squared-L2 radius chosen so that
+~60% of the queries match nothing.  --config c1 runs the 10^6-point workload.
 
 Metric: range QPS at average precision >= 0.95 (Def. 2.2).  As in the paper's
 evaluation (Sec. 5: sweep the starting beam, report the Pareto frontier), the
@@ -144,44 +145,74 @@ def peaks():
     return 6800.0, "fallback"
 
 
+# The form the GPU arm selects at AP >= 0.95 on each workload (from its own sweep); the reference arm, which
+# runs no sweep, times the oracle on that form.
+REF_FORM = {"c1": ("greedy", 192), "c3": ("greedy", 128), "c2": ("greedy_es", 8), "c0": ("greedy", 64)}
+
+
+def oracle_sample(nq, k, seed=5):
+    """A seeded uniform sample of k query indices (the batch's mix: zero-result and heavy-tailed alike)."""
+    return np.sort(np.random.default_rng(seed).permutation(nq)[:min(k, nq)])
+
+
+def cpu_sample_sizes(args, nq):
+    """(all-cores, single-thread) sample sizes: about 10-20 s of oracle time each on 16 host cores."""
+    k_all = args.cpu_sample or (nq if nq <= 10_000 else 2_000)
+    k_one = args.cpu_sample1 or max(1, k_all // 10)
+    return k_all, k_one
+
+
+def time_oracle(oi, ds, idx, variant, beam, threads, vl=20, esr=1.0):
+    import oracle
+    tc = time.perf_counter()
+    oracle.range_search(oi, ds.Q[idx], ds.radius, variant, beam=beam, threads=threads, es_vl=vl,
+                        es_radius=None if not variant.endswith("_es") else float(ds.radius) * esr)
+    return time.perf_counter() - tc
+
+
 def run_reference(args, cfg, ds):
-    """The oracle (plain C, Alg. 6's parallel for over host cores) on a bounded sample per step."""
+    """The oracle (plain C, Alg. 6's parallel for over the host cores), each step a seeded sample of the
+    workload's queries (disjoint slices of one seeded permutation)."""
     import oracle
     ws, rank, _ = dist_env()
     if rank != 0:
         return
     oi = oracle.Index(ds.X, ds.adj, ds.start, metric=oracle.IP if cfg.metric == rrsynth.M_IP else oracle.L2)
-    variant, beam = args.ref_variant, args.ref_beam
+    variant, beam = REF_FORM.get(cfg.name, ("greedy", 64))
+    if args.ref_variant:
+        variant = args.ref_variant
+    if args.ref_beam:
+        beam = args.ref_beam
     cores = os.cpu_count() or 1
-    sample = args.ref_sample
-    Q = ds.Q[:sample]
-    for _ in range(args.warmup if args.warmup < 1 else 1):
-        oracle.range_search(oi, Q[: max(1, sample // 10)], ds.radius, variant, beam=beam, threads=cores)
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        oracle.range_search(oi, Q, ds.radius, variant, beam=beam, threads=cores)
-    dt = time.perf_counter() - t0
-    qps = args.steps * sample / dt
+    nq = len(ds.Q)
+    k = args.ref_sample or (nq // 20 if nq <= 10_000 else 300)
+    order = np.random.default_rng(5).permutation(nq)
+    time_oracle(oi, ds, np.sort(order[:max(1, k // 10)]), variant, beam, cores)  # warm-up
+    dt = 0.0
+    done = 0
+    for s in range(args.steps):
+        idx = np.sort(order[(s * k) % nq:][:k])
+        dt += time_oracle(oi, ds, idx, variant, beam, cores)
+        done += len(idx)
+    qps = done / dt
     line = {"metric": "range QPS at AP>=0.95", "value": qps, "unit": "queries/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1000 * dt / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-            "impl": "reference",
+            "scaling": "weak", "vs_baseline": None, "dtype": "int64" if cfg.dtype == "u8" else "f64",
+            "data": "synthetic", "impl": "reference",
             "config": {"workload": cfg.name + ": n=%d d=%d %s, nq=%d, R=%d" % (
                 cfg.n, cfg.d, "uint8" if cfg.dtype == "u8" else "fp32", cfg.nq, cfg.R),
                        "variant": variant, "beam": beam},
             "cpu_baseline": {"value": qps, "unit": "queries/s", "cores": cores, "kind": "oracle",
-                             "sample": "first %d of the %d queries per step, %s b=%d" % (sample, cfg.nq, variant, beam)},
+                             "sample": "per step %d queries: disjoint slices of one seeded permutation of the %d "
+                                       "(the batch's mix), %s b=%d" % (k, nq, variant, beam)},
             "e2e": {"value": qps, "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
-def run_serve(args, cfg, ds, rr, gi, stream, dev):
-    """Serving leg: open-loop Poisson arrivals of single queries (radii mixed r, 1.5r, 2r) into the
-    continuous-batching server; per offered rate, the achieved rate and submit-to-ready latency."""
+def serve_rates(args, ds, rr, gi, stream, dev, variant, beam, vl, esr, specs, secs):
+    """Open-loop Poisson arrivals of single queries (radii mixed r, 1.5r, 2r) into the continuous-batching
+    server; per offered rate, the achieved rate and submit-to-ready latency.  Returns (batch_qps, rows)."""
     import torch
-    f = (args.fixed or "greedy:192").split(":")
-    variant, beam = f[0], int(f[1])
-    vl, esr = (int(f[2]), float(f[3])) if len(f) > 3 else (20, 1.0)
     base = dict(beam=beam, es_visit_limit=vl, es_radius_mode=1 if variant.endswith("_es") else 0,
                 es_radius=float(ds.radius) * esr)
     nq = len(ds.Q)
@@ -213,11 +244,11 @@ def run_serve(args, cfg, ds, rr, gi, stream, dev):
     log("serve: batch throughput of %s b=%d on the radius mix: %.0f QPS" % (variant, beam, batch_qps))
     rows = []
     Qh = np.ascontiguousarray(ds.Q)
-    for spec in [float(x) for x in args.serve.split(",") if x]:
+    for spec in specs:
         # a value <= 1 is a fraction of the batch throughput, a larger one an absolute rate (QPS)
         rate = spec * batch_qps if spec <= 1.0 else spec
         frac = rate / batch_qps
-        n_arr = int(rate * args.serve_secs)
+        n_arr = max(1, int(rate * secs))
         gaps = rs.exponential(1.0 / rate, n_arr)
         t_arr = np.cumsum(gaps)
         pick = rs.integers(0, nq, n_arr)
@@ -270,8 +301,8 @@ def run_serve(args, cfg, ds, rr, gi, stream, dev):
         with lock:
             done["gen"] = True
             lock.notify()
-        # the window closes serve_secs after the last arrival: what is still queued then is dropped
-        th.join(timeout=args.serve_secs)
+        # the window closes `secs` after the last arrival: what is still queued then is dropped
+        th.join(timeout=secs)
         dropped = rr.rr_serve_cancel(srv.h) if th.is_alive() else 0
         th.join()
         sst = rr.rr_serve_stats(srv.h).as_dict()
@@ -283,10 +314,21 @@ def run_serve(args, cfg, ds, rr, gi, stream, dev):
                "admission_waits": sst["admission_waits"],
                "p50_us": sst["p50_us"], "p99_us": sst["p99_us"], "mean_us": sst["mean_us"], "max_us": sst["max_us"],
                "mean_batch": sst["mean_batch"], "batches": sst["batches"], "requests": collected[0],
-               "results": collected[1], "results_per_served_request": collected[1] / max(1, served), "generator_lag_p99_us": float(np.percentile(lag, 99) * 1e6) if lag else 0.0}
+               "results": collected[1], "results_per_served_request": collected[1] / max(1, served),
+               "generator_lag_p99_us": float(np.percentile(lag, 99) * 1e6) if lag else 0.0}
         rows.append(row)
         log("serve: offered %.0f QPS (%.2f of batch) -> %.0f QPS, p50 %.0f us, p99 %.0f us, mean batch %.0f, "
             "canceled %d" % (rate, frac, row["achieved_qps"], row["p50_us"], row["p99_us"], row["mean_batch"], dropped))
+    return batch_qps, rows
+
+
+def run_serve(args, cfg, ds, rr, gi, stream, dev):
+    """Serving leg: the serving measurement alone, at the offered rates of --serve, as its own JSON line."""
+    f = (args.fixed or "greedy:128").split(":")
+    variant, beam = f[0], int(f[1])
+    vl, esr = (int(f[2]), float(f[3])) if len(f) > 3 else (20, 1.0)
+    batch_qps, rows = serve_rates(args, ds, rr, gi, stream, dev, variant, beam, vl, esr,
+                                  [float(x) for x in args.serve.split(",") if x], args.serve_secs)
     line = {"metric": "serving latency under open-loop Poisson load", "unit": "us", "higher_is_better": False,
             "value": rows[-1]["p99_us"] if rows else None, "n_gpus": 1, "dtype": str(ds.X.dtype), "data": "synthetic",
             "config": {"workload": "%s: n=%d d=%d, single-query requests, radii r/1.5r/2r" % (cfg.name, cfg.n, cfg.d),
@@ -392,16 +434,17 @@ def run_experiments(args, cfg, ds, rr, gi, stream, dev):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="own", choices=["own", "reference"])
-    ap.add_argument("--config", default="c1")
+    ap.add_argument("--config", default="c3")
     ap.add_argument("--variants", default=",".join(VARIANTS))
     ap.add_argument("--beams", default=",".join(map(str, BEAMS)))
-    ap.add_argument("--cpu-sample", type=int, default=0, help="queries for the cpu_baseline leg (0 = auto)")
-    ap.add_argument("--ref-variant", default="greedy", help="the form the GPU arm picks on C1 (AP >= 0.95)")
-    ap.add_argument("--ref-beam", type=int, default=192)
-    ap.add_argument("--ref-sample", type=int, default=300)
+    ap.add_argument("--cpu-sample", type=int, default=0, help="queries for the all-cores oracle timing (0 = auto)")
+    ap.add_argument("--cpu-sample1", type=int, default=0, help="queries for the single-thread oracle timing (0 = auto)")
+    ap.add_argument("--ref-variant", default="", help="reference arm: the form to time (default: the GPU arm's choice)")
+    ap.add_argument("--ref-beam", type=int, default=0)
+    ap.add_argument("--ref-sample", type=int, default=0, help="reference arm: queries per step (0 = auto)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--fixed", default="", help="VARIANT:BEAM[:VL:ESR] -- skip the sweep and time this form")
     ap.add_argument("--no-tune", action="store_true", help="keep the library's default launch shape")
@@ -414,6 +457,9 @@ def main():
     ap.add_argument("--serve-max-batch", type=int, default=4096)
     ap.add_argument("--serve-wait-us", type=int, default=100)
     ap.add_argument("--serve-device", type=int, default=1, choices=[0, 1], help="serving results in device memory")
+    ap.add_argument("--line-serve", default="0.25,0.5",
+                    help="offered rates (fractions of batch QPS) measured for the main line's serving keys ('' = none)")
+    ap.add_argument("--line-serve-secs", type=float, default=2.0)
     ap.add_argument("--experiments", action="store_true", help="phase breakdown per variant and a radius sweep")
     ap.add_argument("--exp-beam", type=int, default=64)
     ap.add_argument("--exp-radii", default="0.5,0.75,1.0,1.5,2.0")
@@ -454,13 +500,19 @@ def main():
     Qd = torch.from_numpy(ds.Q).to("cuda:%d" % dev)
     nq = Qd.shape[0]
 
-    # ground truth: the library's exhaustive search (Def. 2.1)
+    # ground truth: the library's exhaustive search (Def. 2.1), in chunks
     tt = time.time()
-    gt = gi.brute_force(ds.Q, ds.radius)
-    truth = csr_keys(gt.offsets, gt.ids, ds.X.shape[0])
+    parts = []
+    for s0 in range(0, nq, 1 << 15):
+        g = gi.brute_force(Qd[s0:s0 + (1 << 15)], ds.radius)
+        parts.append((np.diff(g.offsets), g.ids))
+    gt_counts = np.concatenate([c for c, _ in parts])
+    gt_offsets = np.concatenate([[0], np.cumsum(gt_counts)])
+    truth = csr_keys(gt_offsets, np.concatenate([i for _, i in parts]), ds.X.shape[0])
+    del parts
     if rank == 0:
-        log("ground truth in %.1fs: %d results, zero-result fraction %.3f" % (
-            time.time() - tt, len(truth), float(np.mean(np.diff(gt.offsets) == 0))))
+        log("ground truth in %.1fs: %d results, zero-result fraction %.3f, max %d" % (
+            time.time() - tt, len(truth), float(np.mean(gt_counts == 0)), int(gt_counts.max())))
 
     def params(form, beam, **kw):
         variant, vl, esr = form
@@ -518,6 +570,8 @@ def main():
                     break  # larger beams only cost more once the target is met
             if form[0].endswith("_es") and abs(apv - last_ap) < 1e-4 and apv < AP_TARGET and beam >= 64:
                 break  # early stop caps this form's precision: more beam does not help
+            if ms > 2000.0:
+                break  # a form this slow cannot be the fastest one at the target
             last_ap = apv
     ok = [s for s in sweep if s["ap"] >= AP_TARGET]
     if not ok:
@@ -601,8 +655,9 @@ def main():
     clocks = clk.summary()
     value = ws * nq / (step_ms / 1000.0)
 
-    # the same form in the plain launch: one warp per query over a full grid, library default shape,
-    # exact arithmetic (the chosen form's batching and precision choices switched off)
+    # the plain GPU form: the same variant and b in one launch per batch (one warp per query over a full
+    # grid, the library's default shape) with exact arithmetic -- the chosen form's batching and precision
+    # choices switched off
     plain_ms = time_form(form, beam, reps=max(3, min(args.steps, 20)), base={"precision": 0})
 
     # end to end through the public API with host buffers: pinned queries in, host CSR out
@@ -623,40 +678,62 @@ def main():
     achieved = bytes_beam / (kern_ms / 1000.0) / 1e9
     whole = bytes_all / (step_ms / 1000.0) / 1e9
 
+    # serving on the same index: single-query requests with radii mixed r / 1.5r / 2r, open-loop Poisson
+    serve = None
+    if rank == 0 and args.line_serve:
+        batch_qps, srows = serve_rates(args, ds, rr, gi, stream, dev, variant, beam, form[1], form[2],
+                                       [float(x) for x in args.line_serve.split(",") if x], args.line_serve_secs)
+        serve = {"what": "single-query requests, radii drawn from r / 1.5r / 2r, open-loop Poisson arrivals for "
+                         "%.1f s per rate, %s b=%d, %d workers, batches up to %d" % (
+                             args.line_serve_secs, variant, beam, args.serve_workers, args.serve_max_batch),
+                 "batch_qps_on_this_mix": batch_qps,
+                 "rates": [{"offered_qps": r["offered_qps"], "achieved_qps": r["achieved_qps"],
+                            "p50_ms": r["p50_us"] / 1000, "p99_ms": r["p99_us"] / 1000, "canceled": r["canceled"],
+                            "mean_batch": r["mean_batch"]} for r in srows]}
+
     cpu = None
     if rank == 0 and not args.no_cpu:
         import oracle
         oi = oracle.Index(ds.X, ds.adj, ds.start, metric=oracle.IP if cfg.metric == rrsynth.M_IP else oracle.L2)
         cores = os.cpu_count() or 1
-        sample = args.cpu_sample or 200
-        tc = time.perf_counter()
-        oracle.range_search(oi, ds.Q[:sample], ds.radius, variant, beam=beam, threads=cores, es_vl=form[1],
-                            es_radius=float(ds.radius) * form[2])
-        dt = time.perf_counter() - tc
-        cpu = {"value": sample / dt, "unit": "queries/s", "cores": cores, "kind": "oracle",
-               "sample": "first %d of the %d queries, %s b=%d, one pass" % (sample, nq, variant, beam)}
+        k_all, k_one = cpu_sample_sizes(args, nq)
+        idx_all = oracle_sample(nq, k_all)
+        idx_one = oracle_sample(nq, k_one)
+        dt_all = time_oracle(oi, ds, idx_all, variant, beam, cores, form[1], form[2])
+        dt_one = time_oracle(oi, ds, idx_one, variant, beam, 1, form[1], form[2])
+        cpu = {"value": len(idx_all) / dt_all, "unit": "queries/s", "cores": cores, "kind": "oracle",
+               "sample": "seeded uniform sample of %d of the %d queries (the batch's mix), %s b=%d, one pass" % (
+                   len(idx_all), nq, variant, beam),
+               "single_thread": {"value": len(idx_one) / dt_one, "unit": "queries/s", "cores": 1,
+                                 "sample": "seeded uniform sample of %d of the %d queries" % (len(idx_one), nq)}}
 
     if rank == 0:
+        plain_qps = ws * nq / (plain_ms / 1000.0)
         line = {
             "metric": "range QPS at AP>=0.95", "value": value, "unit": "queries/s", "n_gpus": ws,
             "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": step_ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "data": "synthetic",
             "dtype": "u8" if ds.X.dtype == np.uint8 else ["f32", "bf16+f32", "fp8+f32"][args.precision],
-            "config": {"workload": "%s: n=%d d=%d %s %s, nq=%d per GPU, Vamana R=%d L=%d alpha=%.2f" % (
+            "config": {"workload": "%s: n=%d d=%d %s %s, nq=%d per GPU, Vamana R=%d L=%d alpha=%.2f passes=%d" % (
                 cfg.name, cfg.n, cfg.d, "uint8" if ds.X.dtype == np.uint8 else "fp32",
-                "IP" if cfg.metric == rrsynth.M_IP else "L2", cfg.nq, cfg.R, cfg.L_build, cfg.alpha),
+                "IP" if cfg.metric == rrsynth.M_IP else "L2", cfg.nq, cfg.R, cfg.L_build, cfg.alpha, cfg.passes),
                 "precision": ["exact", "bf16 traversal, exact fp32 recheck", "fp8-e4m3 traversal, exact fp32 recheck"][
                     args.precision],
                 "variant": variant, "beam": beam, "ap": best["ap"], "es_vl": form[1], "es_radius_over_r": form[2],
                 "launch_shape": tuned or "library default",
-                "plain_launch": {"what": "same variant and b, one warp per query, default shape, exact",
-                                 "ms_per_step": plain_ms, "qps": ws * nq / (plain_ms / 1000.0),
-                                 "chosen_over_plain": plain_ms / step_ms},
                 "beam_phase_evals_per_distinct": float(st_beam["evals"].sum()) / max(1, int(st_beam["distinct"].sum())),
                 "plain_beam_form": None if plain_best is None else {
                     "beam": plain_best["beam"], "qps": plain_best["qps"], "ap": plain_best["ap"]},
                 "l2_policy": "index (vectors + adjacency %.0f MB) larger than L2" % (
                     (ds.X.nbytes + ds.adj.nbytes) / 1e6)},
+            "plain_qps": plain_qps,
+            "chosen_over_plain": plain_ms / step_ms,
+            "plain_what": "same variant and b, one launch per batch over a full grid (one warp per query), the "
+                          "library's default launch shape, exact arithmetic",
+            "serve_p50_ms": serve["rates"][0]["p50_ms"] if serve and serve["rates"] else None,
+            "serve_p99_ms": serve["rates"][0]["p99_ms"] if serve and serve["rates"] else None,
+            "serve_qps": serve["rates"][0]["achieved_qps"] if serve and serve["rates"] else None,
+            "serving": serve,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                          "frac": achieved / hbm,
                          "traffic": MEASURED_TRAFFIC.get((cfg.name, variant, beam)), "kernel": "beam phase (Alg. 1 + Alg. 5)",
