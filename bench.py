@@ -150,16 +150,22 @@ def peaks():
 REF_FORM = {"c1": ("greedy", 192), "c3": ("greedy", 128), "c2": ("greedy_es", 8), "c0": ("greedy", 64)}
 
 
-def oracle_sample(nq, k, seed=5):
-    """A seeded uniform sample of k query indices (the batch's mix: zero-result and heavy-tailed alike)."""
-    return np.sort(np.random.default_rng(seed).permutation(nq)[:min(k, nq)])
-
-
-def cpu_sample_sizes(args, nq):
-    """(all-cores, single-thread) sample sizes: about 10-20 s of oracle time each on 16 host cores."""
-    k_all = args.cpu_sample or (nq if nq <= 10_000 else 2_000)
-    k_one = args.cpu_sample1 or max(1, k_all // 10)
-    return k_all, k_one
+def timed_oracle_sample(oi, ds, variant, beam, threads, vl, esr, fixed, budget_s=12.0, seed=5):
+    """Time the oracle on a seeded uniform sample of the queries, sized to about budget_s seconds: a pilot
+    of 8 queries per thread, then the rest of a sample scaled from the pilot's rate (or `fixed` queries).
+    Returns (queries timed, seconds)."""
+    nq = len(ds.Q)
+    order = np.random.default_rng(seed).permutation(nq)
+    if fixed:
+        idx = np.sort(order[:min(fixed, nq)])
+        return len(idx), time_oracle(oi, ds, idx, variant, beam, threads, vl, esr)
+    k0 = min(nq, 8 * threads)
+    t0 = time_oracle(oi, ds, np.sort(order[:k0]), variant, beam, threads, vl, esr)
+    k = int(min(nq, max(k0, k0 * budget_s / max(t0, 1e-3))))
+    if k <= k0:
+        return k0, t0
+    t1 = time_oracle(oi, ds, np.sort(order[k0:k]), variant, beam, threads, vl, esr)
+    return k, t0 + t1
 
 
 def time_oracle(oi, ds, idx, variant, beam, threads, vl=20, esr=1.0):
@@ -572,6 +578,9 @@ def main():
                 break  # early stop caps this form's precision: more beam does not help
             if ms > 2000.0:
                 break  # a form this slow cannot be the fastest one at the target
+            best_ok = max([x["qps"] for x in sweep if x["ap"] >= AP_TARGET], default=0.0)
+            if nq / (ms / 1000) < best_ok:
+                break  # QPS falls as b grows: this form cannot overtake the fastest one at the target
             last_ap = apv
     ok = [s for s in sweep if s["ap"] >= AP_TARGET]
     if not ok:
@@ -696,16 +705,15 @@ def main():
         import oracle
         oi = oracle.Index(ds.X, ds.adj, ds.start, metric=oracle.IP if cfg.metric == rrsynth.M_IP else oracle.L2)
         cores = os.cpu_count() or 1
-        k_all, k_one = cpu_sample_sizes(args, nq)
-        idx_all = oracle_sample(nq, k_all)
-        idx_one = oracle_sample(nq, k_one)
-        dt_all = time_oracle(oi, ds, idx_all, variant, beam, cores, form[1], form[2])
-        dt_one = time_oracle(oi, ds, idx_one, variant, beam, 1, form[1], form[2])
-        cpu = {"value": len(idx_all) / dt_all, "unit": "queries/s", "cores": cores, "kind": "oracle",
-               "sample": "seeded uniform sample of %d of the %d queries (the batch's mix), %s b=%d, one pass" % (
-                   len(idx_all), nq, variant, beam),
-               "single_thread": {"value": len(idx_one) / dt_one, "unit": "queries/s", "cores": 1,
-                                 "sample": "seeded uniform sample of %d of the %d queries" % (len(idx_one), nq)}}
+        k_all, dt_all = timed_oracle_sample(oi, ds, variant, beam, cores, form[1], form[2], args.cpu_sample)
+        k_one, dt_one = timed_oracle_sample(oi, ds, variant, beam, 1, form[1], form[2], args.cpu_sample1,
+                                            seed=6)
+        cpu = {"value": k_all / dt_all, "unit": "queries/s", "cores": cores, "kind": "oracle",
+               "sample": "seeded uniform sample of %d of the %d queries (the batch's mix), %s b=%d, one pass, "
+                         "sized to ~12 s" % (k_all, nq, variant, beam),
+               "single_thread": {"value": k_one / dt_one, "unit": "queries/s", "cores": 1,
+                                 "sample": "seeded uniform sample of %d of the %d queries, sized to ~12 s" % (
+                                     k_one, nq)}}
 
     if rank == 0:
         plain_qps = ws * nq / (plain_ms / 1000.0)

@@ -108,11 +108,14 @@ def test_c1_graph_identical(rr):
 
 
 def test_c3_recipe_sample_identical(rr):
-    """200,000 points of the 10^7-point recipe (d = 256, R = 64, L = 128, alpha = 1.2, two passes)."""
-    cfg = dataclasses.replace(rrsynth.CONFIGS["c3"], name="c3_sample", n=200_000, nq=100, n_centres=500,
-                              fam_cap=2000, builder="cpu", streams=0)
-    ds = rrsynth.make_dataset(cfg, cache_dir=CACHE)
-    gpu, info = rr.rr_build_graph(ds.X, cfg.R, cfg.L_build, cfg.alpha, passes=cfg.passes, seed=cfg.seed,
-                                  start=ds.start)
-    diff = np.nonzero((gpu != ds.adj).any(1))[0]
-    assert len(diff) == 0, "%d rows differ, first %d" % (len(diff), diff[0])
+    """200,000 points of the 10^7-point recipe (d = 256, R = 64, alpha = 1.2, two passes), with the
+    10^7-point graph's L = 48 and with L = 128."""
+    for L in (48, 128):
+        cfg = dataclasses.replace(rrsynth.CONFIGS["c3"], name="c3_sample_L%d" % L, n=200_000, nq=100,
+                                  n_centres=500, fam_cap=2000, builder="cpu", streams=0, L_build=L)
+        ds = rrsynth.make_dataset(cfg, cache_dir=CACHE)
+        gpu, info = rr.rr_build_graph(ds.X, cfg.R, cfg.L_build, cfg.alpha, passes=cfg.passes, seed=cfg.seed,
+                                      start=ds.start)
+        diff = np.nonzero((gpu != ds.adj).any(1))[0]
+        assert len(diff) == 0, "L=%d: %d rows differ, first %d" % (L, len(diff), diff[0])
+

@@ -4,8 +4,9 @@ The search traverses an fp32 index exactly, through a BF16 copy, or through an
 FP8-e4m3 copy with per-vector scales; every in-range decision is re-made in
 exact fp32.  Floating-point traversal changes the visit order, so parity with
 the fp64 oracle is statistical: average precision against exhaustive ground
-truth (Def. 2.2) within 0.002 of the oracle's, every returned distance within
-1e-5 relative of an fp64 recomputation, every returned point truly in range."""
+truth (Def. 2.2) within 0.002 of the oracle's on a 2,000-query fixture, every
+returned distance within 1e-5 relative of an fp64 recomputation, every
+returned point truly in range."""
 import dataclasses
 import os
 
@@ -50,13 +51,25 @@ def setup(request):
     import paper_2502_13245_gb300 as rr
     rr.build()
     metric = rrsynth.M_IP if request.param == "ip" else rrsynth.M_L2
-    cfg = dataclasses.replace(rrsynth.CONFIGS["c2"], name="c2s_" + request.param, n=100_000, nq=500, passes=1,
+    cfg = dataclasses.replace(rrsynth.CONFIGS["c2"], name="c2s_" + request.param, n=100_000, nq=2_000, passes=1,
                               n_centres=100, metric=metric, alpha=1.0 if metric == rrsynth.M_IP else 1.2)
     ds = rrsynth.make_dataset(cfg, cache_dir=CACHE)
     gi = rr.Index.from_arrays(ds.X, ds.adj, ds.start, metric=rr.RR_IP if metric == rrsynth.M_IP else rr.RR_L2)
     oi = oracle.Index(ds.X, ds.adj, ds.start, metric=oracle.IP if metric == rrsynth.M_IP else oracle.L2)
     truth = _truth(ds, metric)
     return rr, ds, gi, oi, truth, metric
+
+
+_oracle_ap = {}
+
+
+def _oracle_ap_of(ds, oi, truth, variant, beam):
+    key = (ds.cfg.name, variant, beam)
+    if key not in _oracle_ap:
+        o_ids, _, _ = oracle.range_search(oi, ds.Q, float(ds.radius), variant, beam=beam,
+                                          threads=os.cpu_count() or 4)
+        _oracle_ap[key] = oracle.average_precision(truth, o_ids)
+    return _oracle_ap[key]
 
 
 @pytest.mark.parametrize("prec", ["exact", "bf16", "fp8"])
@@ -77,12 +90,12 @@ def test_precision_form(setup, prec, variant, beam):
         np.testing.assert_allclose(d.astype(np.float64), ex, rtol=1e-5, atol=1e-6)
         assert np.all(ex <= r + 1e-5 * abs(r) + 1e-6)
         assert np.all(np.diff(d) >= 0)  # sorted by distance
-    o_ids, _, _ = oracle.range_search(oi, ds.Q, r, variant, beam=beam, threads=os.cpu_count() or 4)
     ap_gpu = oracle.average_precision(truth, found)
-    ap_oracle = oracle.average_precision(truth, o_ids)
-    # Exact fp32 and BF16 traversal stay within 0.002 of the fp64 oracle.  FP8's ~6% per-element
-    # rounding changes the visit order; on this 500-query sample a handful of heavy queries carry
-    # most of the (micro-averaged) AP, and whether their first beam comes back full (|N| = b, the
-    # phase-2 trigger of Alg. 6 / Alg. 3) flips with the order -- so FP8 under L2 is held to 0.15.
-    tol = 0.15 if (prec == "fp8" and metric == rrsynth.M_L2) else 0.002
-    assert abs(ap_gpu - ap_oracle) <= tol, (prec, variant, ap_gpu, ap_oracle)
+    ap_oracle = _oracle_ap_of(ds, oi, truth, variant, beam)
+    # AP (Def. 2.2) within 0.002 of the fp64 oracle's.  Exact fp32 and BF16 traversal follow the
+    # oracle's visit order closely: two-sided.  FP8-e4m3's coarser traversal distances change the
+    # visit order, which can find more as well as less: the bound holds on the loss.
+    if prec == "fp8":
+        assert ap_gpu >= ap_oracle - 0.002, (prec, variant, ap_gpu, ap_oracle)
+    else:
+        assert abs(ap_gpu - ap_oracle) <= 0.002, (prec, variant, ap_gpu, ap_oracle)
