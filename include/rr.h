@@ -97,7 +97,12 @@ typedef struct {
     int32_t profile;           /* 1: record per-phase device times, see rr_last_profile */
     int32_t seen_log2;         /* log2 slots of the beam kernel's seen table, 5..14 (0 = library choice) */
     int32_t es_metric;         /* the M of Alg. 4 (Sec. 3.2), see rr_es_metric; RR_ES_VISITED is Alg. 5 */
-    int32_t reserved[4];
+    int32_t expand;            /* parents per BeamSearch iteration, 1..4 (0 or 1 = Alg. 1 itself; beam and
+                                  greedy variants only).  expand = E > 1 is a variant of Alg. 1 that is not
+                                  in the paper: each iteration visits the E closest unvisited points of B
+                                  at once (Alg. 5 tests the first), adds the out-neighbours of all of them
+                                  that are not in V or B, then trims B to b once */
+    int32_t reserved[3];
 } rr_params;
 
 /* Early-stopping metrics (Sec. 3.2; Alg. 4 with this M replacing Alg. 5's last

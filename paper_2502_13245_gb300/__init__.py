@@ -50,7 +50,7 @@ class Params(ctypes.Structure):
                 ("recheck_eps", ctypes.c_float), ("persistent", ctypes.c_int32), ("collect_stats", ctypes.c_int32),
                 ("max_results_total", ctypes.c_int64), ("tile_hint", ctypes.c_int32),
                 ("profile", ctypes.c_int32), ("seen_log2", ctypes.c_int32), ("es_metric", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 4)]
+                ("expand", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
 
 
 class Profile(ctypes.Structure):

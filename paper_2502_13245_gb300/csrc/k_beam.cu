@@ -80,7 +80,7 @@ __global__ void __launch_bounds__(256, kBeamMinBlocks<DT>) beam_kernel(SearchArg
     extern __shared__ __align__(16) uint8_t smem_raw[];
     const int lane = lane_id();
     const int warp = threadIdx.x >> 5;
-    uint8_t *base = smem_raw + (size_t)warp * warp_smem_bytes(BMAX, a.R, hlg);
+    uint8_t *base = smem_raw + (size_t)warp * warp_smem_bytes(BMAX, a.R * (a.expand > 1 ? a.expand : 1), hlg);
     int64_t qi = 0;
     if (!persistent) qi = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
     else if (lane == 0) qi = atomicAdd(next_q, 1);
@@ -102,14 +102,16 @@ __device__ __forceinline__ void search_query(const SearchArgs &a, int hlg, int64
     const int R = a.R;
     const int b = a.beam;
     const int H = 1 << hlg;
+    const int E = a.expand > 1 ? a.expand : 1;  // parents per iteration (1: Alg. 1)
+    const int ER = R * E;
 
     uint64_t *B = reinterpret_cast<uint64_t *>(base);
     uint64_t *ckey = B + BMAX;       // candidate keys, then the sorted survivors
-    uint64_t *skey = ckey + R;       // survivors before sorting
-    uint32_t *cid = reinterpret_cast<uint32_t *>(skey + R);
-    int32_t *lbs = reinterpret_cast<int32_t *>(cid + R);  // insertion point of each sorted survivor
-    int32_t *slb = lbs + R;                                // insertion point of each unsorted survivor
-    uint32_t *hash = reinterpret_cast<uint32_t *>(slb + R);
+    uint64_t *skey = ckey + ER;      // survivors before sorting
+    uint32_t *cid = reinterpret_cast<uint32_t *>(skey + ER);
+    int32_t *lbs = reinterpret_cast<int32_t *>(cid + ER);  // insertion point of each sorted survivor
+    int32_t *slb = lbs + ER;                                // insertion point of each unsorted survivor
+    uint32_t *hash = reinterpret_cast<uint32_t *>(slb + ER);
 
     constexpr bool LP = is_lowp(DT);
     uint4 q[CPL];
@@ -175,14 +177,31 @@ __device__ __forceinline__ void search_query(const SearchArgs &a, int hlg, int64
             break;
         }
         __syncwarp();
+        // the parents of this iteration: p* and, with E > 1, the next E - 1 unvisited entries of B
+        int par[3] = {-1, -1, -1};
+        int np = 1;
+        for (int b0 = cur + 1; b0 < nb && np < E; b0 += 32) {
+            const int i = b0 + lane;
+            unsigned m = __ballot_sync(0xffffffffu, i < nb && !(B[i] & 1ull));
+            while (m && np < E) {
+                const int pos = b0 + __ffs(m) - 1;
+                m &= m - 1;
+                par[np - 1] = pos;
+                np++;
+            }
+        }
+        uint32_t pid[3] = {kSent, kSent, kSent};
+        for (int e = 1; e < np; e++) pid[e - 1] = key_id(B[par[e - 1]]);
+        __syncwarp();
         if (lane == 0) {
             B[cur] = pk | 1ull;  // V <- V u {p*}
             if (BUILD && nvis < a.vis_cap) a.vis_out[(size_t)qi * a.vis_cap + nvis] = pk & ~1ull;
+            for (int e = 1; e < np; e++) B[par[e - 1]] |= 1ull;
         }
-        nvis++;
+        nvis += np;
         __syncwarp();
         const int nxt = next_unvisited(B, nb, cur + 1);
-        // N_out(p*) minus ids seen before (see the file comment)
+        // N_out of the parents minus ids seen before (see the file comment)
         uint32_t row4[4];
         if (p == pre_id) {
 #pragma unroll
@@ -203,27 +222,36 @@ __device__ __forceinline__ void search_query(const SearchArgs &a, int hlg, int64
             }
         }
         int nc = 0;
+        for (int e = 0; e < np; e++) {
+            if (e > 0) {
+                const uint32_t pe = pid[e - 1];
+                if (pe >= (uint32_t)a.n) continue;  // cannot happen for a validated index
+                const uint32_t *row = a.adj + (size_t)pe * R;
 #pragma unroll
-        for (int k = 0; k < 4; k++) {
-            if (32 * k >= R) break;  // warp-uniform
-            uint32_t j = row4[k];
-            bool v = j < (uint32_t)a.n;  // also drops the 0xFFFFFFFF padding
-            uint32_t sl = 0, old = kSent;
-            if (v) {
-                // two-way set: slot 2s holds the most recent id of the set, 2s+1 the one before
-                sl = hslot(j, hlg - 1) << 1;
-                old = hash[sl];
-                v = old != j && hash[sl + 1] != j;
+                for (int k = 0; k < 4; k++) row4[k] = (32 * k + lane < R) ? __ldg(row + 32 * k + lane) : kSent;
             }
-            unsigned m = __ballot_sync(0xffffffffu, v);
-            __syncwarp();
-            if (v) {
-                hash[sl + 1] = old;
-                hash[sl] = j;
-                cid[nc + __popc(m & lanemask_lt())] = j;
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                if (32 * k >= R) break;  // warp-uniform
+                uint32_t j = row4[k];
+                bool v = j < (uint32_t)a.n;  // also drops the 0xFFFFFFFF padding
+                uint32_t sl = 0, old = kSent;
+                if (v) {
+                    // two-way set: slot 2s holds the most recent id of the set, 2s+1 the one before
+                    sl = hslot(j, hlg - 1) << 1;
+                    old = hash[sl];
+                    v = old != j && hash[sl + 1] != j;
+                }
+                unsigned m = __ballot_sync(0xffffffffu, v);
+                __syncwarp();
+                if (v) {
+                    hash[sl + 1] = old;
+                    hash[sl] = j;
+                    cid[nc + __popc(m & lanemask_lt())] = j;
+                }
+                nc += __popc(m);
+                __syncwarp();
             }
-            nc += __popc(m);
-            __syncwarp();
         }
         if (nc == 0) { cur = nxt; continue; }
         evals += nc;
@@ -257,14 +285,34 @@ __device__ __forceinline__ void search_query(const SearchArgs &a, int hlg, int64
         }
         __syncwarp();
         if (ns == 0) { cur = nxt; continue; }
+        int nsu = ns;
+        if (E > 1) {
+            // with several parents, a neighbour the lossy table forgot within this iteration can come
+            // twice: keep the first copy of each key (B stays a set)
+            nsu = 0;
+            for (int c0 = 0; c0 < ns; c0 += 32) {
+                const int c = c0 + lane;
+                bool first = c < ns;
+                if (first) {
+                    const uint64_t k = skey[c];
+                    for (int t = 0; t < c && first; t++) first = skey[t] != k;
+                }
+                nsu += __popc(__ballot_sync(0xffffffffu, first));
+                if (c < ns && !first) slb[c] = -1;
+            }
+            __syncwarp();
+        }
         // sort the survivors (distinct keys) by rank; each keeps its insertion point in B
         for (int c = lane; c < ns; c += 32) {
+            const int lbc = slb[c];
+            if (lbc < 0) continue;
             uint64_t k = skey[c];
             int r = 0;
-            for (int t = 0; t < ns; t++) r += skey[t] < k;
+            for (int t = 0; t < ns; t++) r += (skey[t] < k) && (E == 1 || slb[t] >= 0);
             ckey[r] = k;
-            lbs[r] = slb[c];
+            lbs[r] = lbc;
         }
+        ns = nsu;
         __syncwarp();
         const int lb0 = lbs[0];
         // B <- top-b(B u survivors): shift the suffix [lb0, nb) right, last chunk first
@@ -339,7 +387,7 @@ __device__ __forceinline__ void search_query(const SearchArgs &a, int hlg, int64
 template <int DT, int CPL, int BMAX, bool COUNT>
 rr_status launch_k(const SearchArgs &a, int wpc, int hlg, cudaStream_t st) {
     auto k = beam_kernel<DT, CPL, BMAX, COUNT>;
-    const size_t smem = (size_t)wpc * warp_smem_bytes(BMAX, a.R, hlg);
+    const size_t smem = (size_t)wpc * warp_smem_bytes(BMAX, a.R * std::max(1, a.expand), hlg);
     RR_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int64_t blocks = (a.nq + wpc - 1) / wpc;
     if (a.persistent) {

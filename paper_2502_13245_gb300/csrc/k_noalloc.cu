@@ -128,6 +128,10 @@ extern "C" rr_status rr_beam_search_noalloc(rr_index *ix, const void *queries, i
                   "(es_radius_mode = 1) and needs squared L2");
         return RR_EINVAL;
     }
+    if (P.expand < 0 || P.expand > 4) {
+        set_error("rr_beam_search_noalloc: expand=%d out of [0, 4]", P.expand);
+        return RR_EINVAL;
+    }
     if (P.precision != RR_PREC_EXACT) {
         // the BF16 / FP8 traversal copies are built (allocated) on first use
         set_error("rr_beam_search_noalloc: only exact traversal (precision = RR_PREC_EXACT) allocates nothing");
@@ -203,6 +207,7 @@ extern "C" rr_status rr_beam_search_noalloc(rr_index *ix, const void *queries, i
     a.d = ix->d;
     a.prec = RR_PREC_EXACT;
     a.iter_limit = beam_iteration_limit(ix->n);
+    a.expand = std::max(1, P.expand);
     a.phase2 = 0;
     a.res_keys = (uint64_t *)(S + off_keys);
     a.res_count = (int32_t *)(S + off_cnt);

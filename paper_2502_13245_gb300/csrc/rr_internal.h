@@ -117,6 +117,7 @@ struct SearchArgs {
     int32_t use_es;
     int32_t es_vl;
     int32_t es_metric;        // rr_es_metric (the beam kernel; the doubling kernel takes RR_ES_VISITED)
+    int32_t expand;           // parents per beam-kernel iteration (1 = Alg. 1; the doubling kernel takes 1)
     double es_ratio;          // threshold t of RR_ES_TOP10_RATIO
     int32_t phase2;           // 0 none, 1 greedy, 2 doubling: queries with |N| = b are queued
     // outputs of the beam phase

@@ -492,6 +492,11 @@ extern "C" rr_status rr_range_search(rr_index *ix, const void *queries, int64_t 
         return RR_EINVAL;
     }
     if (doubling && P.b_max < P.beam) { set_error("rr_range_search: b_max < beam"); return RR_EINVAL; }
+    if (P.expand < 0 || P.expand > 4) { set_error("rr_range_search: expand=%d out of [0, 4]", P.expand); return RR_EINVAL; }
+    if (P.expand > 1 && doubling) {
+        set_error("rr_range_search: multi-parent expansion (expand > 1) is for the beam and greedy variants");
+        return RR_EINVAL;
+    }
     DeviceGuard dg(ix->device);
     rr_status s = stage(S, queries, radii, radius, false);
     if (s != RR_OK) return S.fail(s);
@@ -504,6 +509,7 @@ extern "C" rr_status rr_range_search(rr_index *ix, const void *queries, int64_t 
     a.persistent = P.persistent ? 1 : 0;
     a.next_q = a.p2_count + 2;  // zeroed with the other counters in stage()
     a.iter_limit = beam_iteration_limit(ix->n);
+    a.expand = std::max(1, P.expand);
     a.d = ix->d;
     a.prec = RR_PREC_EXACT;
     if (P.precision != RR_PREC_EXACT) {

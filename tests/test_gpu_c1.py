@@ -50,14 +50,16 @@ def test_c1_brute_force_sample(env):
         assert np.array_equal(g_d.astype(np.int64), d.astype(np.int64))
 
 
-@pytest.mark.parametrize("variant,beam,k_heavy,k_rand", [("greedy_es", 16, 20, 80), ("greedy", 64, 10, 40),
-                                                          ("beam_es", 64, 5, 95), ("doubling_es", 16, 6, 34)])
-def test_c1_sampled_bit_exact(env, variant, beam, k_heavy, k_rand):
+@pytest.mark.parametrize("variant,beam,k_heavy,k_rand,expand", [("greedy_es", 16, 20, 80, 1), ("greedy", 64, 10, 40, 1),
+                                                                 ("beam_es", 64, 5, 95, 1), ("doubling_es", 16, 6, 34, 1),
+                                                                 ("greedy", 64, 10, 40, 2)])
+def test_c1_sampled_bit_exact(env, variant, beam, k_heavy, k_rand, expand):
     rr, ds, gi, oi, Qd, gt = env
-    res = gi.range_search(Qd, ds.radius, variant, beam=beam)
+    res = gi.range_search(Qd, ds.radius, variant, beam=beam, expand=expand)
     assert res.status == rr.RR_OK
     sel = _sample(gt, k_heavy, k_rand, 2)
-    o_ids, o_d, o_st = oracle.range_search(oi, ds.Q[sel], ds.radius, variant, beam=beam, threads=os.cpu_count() or 4)
+    o_ids, o_d, o_st = oracle.range_search(oi, ds.Q[sel], ds.radius, variant, beam=beam, expand=expand,
+                                           threads=os.cpu_count() or 4)
     for k, i in enumerate(sel):
         ids, d = res.query(i)
         assert np.array_equal(ids, o_ids[k]), "query %d: %d vs %d results" % (i, len(ids), len(o_ids[k]))

@@ -288,3 +288,30 @@ def test_profiled_calls_are_bit_exact(rr, c0, c0_index, c0_oracle, variant, beam
                 assert pr.phase2_queries == 0 and pr.phase2_steps == 0
         else:
             assert pr.valid == 0
+
+
+@pytest.mark.parametrize("expand", [2, 3, 4])
+@pytest.mark.parametrize("variant,beam", [("beam", 32), ("beam_es", 16), ("greedy", 16), ("greedy_es", 32)])
+def test_c0_multi_parent_bit_exact(rr, c0, c0_index, c0_oracle, variant, beam, expand):
+    """Multi-parent beam search (expand parents per iteration, a variant of Alg. 1 that is not in the
+    paper) against the oracle's own transcription of it: ids, distances, flags and exact counters."""
+    o_ids, o_d, o_st = oracle.range_search(c0_oracle, c0.Q, c0.radius, variant, beam=beam, expand=expand,
+                                           threads=os.cpu_count() or 4)
+    res = c0_index.range_search(c0.Q, c0.radius, variant, beam=beam, expand=expand, collect_stats=1)
+    assert res.status == rr.RR_OK
+    assert_same(res, o_ids, o_d, len(c0.Q))
+    es = np.array([s["early_stopped"] for s in o_st], bool)
+    assert np.array_equal((res.flags & rr.RR_FLAG_EARLY_STOPPED) != 0, es)
+    assert np.array_equal(res.stats["visits_beam"], [s["visits_beam"] for s in o_st])
+    assert np.array_equal(res.stats["distinct"], [s["distinct"] for s in o_st])
+    # persistent launch in another shape: the same results
+    res2 = c0_index.range_search(c0.Q, c0.radius, variant, beam=beam, expand=expand, persistent=1, tile_hint=2,
+                                 seen_log2=7)
+    assert_same(res2, o_ids, o_d, len(c0.Q))
+
+
+def test_multi_parent_arguments_are_checked(rr, c0, c0_index):
+    with pytest.raises(rr.RRError):
+        c0_index.range_search(c0.Q[:4], c0.radius, "doubling", beam=16, expand=2)
+    with pytest.raises(rr.RRError):
+        c0_index.range_search(c0.Q[:4], c0.radius, "greedy", beam=16, expand=5)

@@ -65,7 +65,8 @@ def test_noalloc_matches_range_search_twice_in_a_row():
     for variant, beam, extra in (("beam_es", 32, {}), ("beam", 16, {}),
                                  ("beam_es", 24, {"es_metric": rr.RR_ES_TOP10, "es_radius_mode": 1,
                                                   "es_radius": float(ds.radius) * 1.5, "es_visit_limit": 10}),
-                                 ("beam", 64, {"persistent": 1, "tile_hint": 2, "seen_log2": 9})):
+                                 ("beam", 64, {"persistent": 1, "tile_hint": 2, "seen_log2": 9}),
+                                 ("beam_es", 32, {"expand": 2})):
         total += _check_against_range_search(rr, torch, gi, Qd, ds.radius, variant, beam, False, **extra)
     assert total > 0
     gi.close()
