@@ -148,7 +148,8 @@ def peaks():
 
 # The form the GPU arm selects at AP >= 0.95 on each workload (from its own sweep); the reference arm, which
 # runs no sweep, times the oracle on that form.
-REF_FORM = {"c1": ("greedy", 192), "c3": ("greedy", 128), "c2": ("greedy_es", 8), "c0": ("greedy", 64)}
+REF_FORM = {"c1": ("greedy", 192, 20, 1.0), "c3": ("greedy_es", 96, 100, 2.0), "c2": ("greedy_es", 8, 20, 1.0),
+            "c0": ("greedy", 64, 20, 1.0)}
 
 
 def timed_oracle_sample(oi, ds, variant, beam, threads, vl, esr, fixed, budget_s=12.0, seed=5):
@@ -185,21 +186,21 @@ def run_reference(args, cfg, ds):
     if rank != 0:
         return
     oi = oracle.Index(ds.X, ds.adj, ds.start, metric=oracle.IP if cfg.metric == rrsynth.M_IP else oracle.L2)
-    variant, beam = REF_FORM.get(cfg.name, ("greedy", 64))
+    variant, beam, vl, esr = REF_FORM.get(cfg.name, ("greedy", 64, 20, 1.0))
     if args.ref_variant:
-        variant = args.ref_variant
+        variant, vl, esr = args.ref_variant, 20, 1.0
     if args.ref_beam:
         beam = args.ref_beam
     cores = os.cpu_count() or 1
     nq = len(ds.Q)
     k = args.ref_sample or (nq // 20 if nq <= 10_000 else 300)
     order = np.random.default_rng(5).permutation(nq)
-    time_oracle(oi, ds, np.sort(order[:max(1, k // 10)]), variant, beam, cores)  # warm-up
+    time_oracle(oi, ds, np.sort(order[:max(1, k // 10)]), variant, beam, cores, vl, esr)  # warm-up
     dt = 0.0
     done = 0
     for s in range(args.steps):
         idx = np.sort(order[(s * k) % nq:][:k])
-        dt += time_oracle(oi, ds, idx, variant, beam, cores)
+        dt += time_oracle(oi, ds, idx, variant, beam, cores, vl, esr)
         done += len(idx)
     qps = done / dt
     line = {"metric": "range QPS at AP>=0.95", "value": qps, "unit": "queries/s", "n_gpus": ws, "steps": args.steps,
@@ -208,7 +209,7 @@ def run_reference(args, cfg, ds):
             "data": "synthetic", "impl": "reference",
             "config": {"workload": cfg.name + ": n=%d d=%d %s, nq=%d, R=%d" % (
                 cfg.n, cfg.d, "uint8" if cfg.dtype == "u8" else "fp32", cfg.nq, cfg.R),
-                       "variant": variant, "beam": beam},
+                       "variant": variant, "beam": beam, "es_vl": vl, "es_radius_over_r": esr},
             "cpu_baseline": {"value": qps, "unit": "queries/s", "cores": cores, "kind": "oracle",
                              "sample": "per step %d queries: disjoint slices of one seeded permutation of the %d "
                                        "(the batch's mix), %s b=%d" % (k, nq, variant, beam)},
@@ -249,6 +250,24 @@ def serve_rates(args, ds, rr, gi, stream, dev, variant, beam, vl, esr, specs, se
     torch.cuda.synchronize()
     batch_qps = done_q / (time.perf_counter() - t0)
     log("serve: batch throughput of %s b=%d on the radius mix: %.0f QPS" % (variant, beam, batch_qps))
+    # what the mix costs: exact counters on a sample of the requests -> algorithmic bytes per request (adjacency
+    # rows of every visit + every distinct vector evaluated + the query) and the request rate at which those
+    # bytes alone would fill the measured HBM bandwidth
+    ns = min(nq, 2048)
+    ps = rr.rr_params_init(max_results_total=1 << 30, collect_stats=1, **base)
+    Qd = torch.from_numpy(ds.Q[:ns]).to("cuda:%d" % dev)
+    st, res = rr.rr_range_search(gi.h, Qd, radii[:ns], variant, ps, stream=stream.cuda_stream, result_on_device=False)
+    rres = rr.RangeResult(res, st)
+    row = ds.X.shape[1] * ds.X.dtype.itemsize
+    R = ds.adj.shape[1]
+    vis = rres.stats["visits_beam"].astype(np.int64) + rres.stats["visits_phase2"].astype(np.int64)
+    req_bytes = float((vis * 4 * R + rres.stats["distinct"].astype(np.int64) * row + row).mean())
+    hbm, _ = peaks()
+    cost = {"sample_requests": ns, "results_per_request": float(len(rres.ids)) / ns,
+            "bytes_per_request": req_bytes, "hbm_bound_qps": hbm * 1e9 / req_bytes,
+            "batch_qps_over_hbm_bound": batch_qps / (hbm * 1e9 / req_bytes)}
+    log("serve: mix costs %.0f results and %.2f MB of gathers per request: HBM bound %.0f QPS" % (
+        cost["results_per_request"], req_bytes / 1e6, cost["hbm_bound_qps"]))
     rows = []
     Qh = np.ascontiguousarray(ds.Q)
     for spec in specs:
@@ -326,7 +345,7 @@ def serve_rates(args, ds, rr, gi, stream, dev, variant, beam, vl, esr, specs, se
         rows.append(row)
         log("serve: offered %.0f QPS (%.2f of batch) -> %.0f QPS, p50 %.0f us, p99 %.0f us, mean batch %.0f, "
             "canceled %d" % (rate, frac, row["achieved_qps"], row["p50_us"], row["p99_us"], row["mean_batch"], dropped))
-    return batch_qps, rows
+    return batch_qps, rows, cost
 
 
 def run_serve(args, cfg, ds, rr, gi, stream, dev):
@@ -334,14 +353,14 @@ def run_serve(args, cfg, ds, rr, gi, stream, dev):
     f = (args.fixed or "greedy:128").split(":")
     variant, beam = f[0], int(f[1])
     vl, esr = (int(f[2]), float(f[3])) if len(f) > 3 else (20, 1.0)
-    batch_qps, rows = serve_rates(args, ds, rr, gi, stream, dev, variant, beam, vl, esr,
-                                  [float(x) for x in args.serve.split(",") if x], args.serve_secs)
+    batch_qps, rows, cost = serve_rates(args, ds, rr, gi, stream, dev, variant, beam, vl, esr,
+                                        [float(x) for x in args.serve.split(",") if x], args.serve_secs)
     line = {"metric": "serving latency under open-loop Poisson load", "unit": "us", "higher_is_better": False,
             "value": rows[-1]["p99_us"] if rows else None, "n_gpus": 1, "dtype": str(ds.X.dtype), "data": "synthetic",
             "config": {"workload": "%s: n=%d d=%d, single-query requests, radii r/1.5r/2r" % (cfg.name, cfg.n, cfg.d),
                        "variant": variant, "beam": beam, "workers": args.serve_workers,
                        "max_batch": args.serve_max_batch, "batch_wait_us": args.serve_wait_us,
-                       "seconds_per_rate": args.serve_secs, "batch_qps": batch_qps,
+                       "seconds_per_rate": args.serve_secs, "batch_qps": batch_qps, "mix_cost": cost,
                        "results_in": "device memory" if args.serve_device else "host memory",
                        "window": "arrivals for seconds_per_rate s, then as long again to drain; still queued then: "
                                  "canceled and not counted; latency = submit to result ready"},
@@ -659,13 +678,15 @@ def main():
         torch.cuda.synchronize()
         torch.cuda.nvtx.range_pop()
     step_ms = e0.elapsed_time(e1) / args.steps
-    beam_ms, per_step = [], []
+    beam_ms, per_step, phase_ms = [], [], []
     for _ in range(5):
         st, res = rr.rr_range_search(gi.h, Qd, ds.radius, variant, pp, stream=sh, result_on_device=True)
         prof = rr.rr_last_profile(gi.h)
         per_step.append(prof.launches)
         beam_ms.append(prof.beam_ms)
+        phase_ms.append((prof.beam_ms, prof.phase2_ms, prof.output_ms, prof.total_ms))
         rr.rr_result_free(res)
+    phase_ms = np.mean(np.asarray(phase_ms), axis=0)
     launches = int(per_step[-1]) * args.steps  # the same batch launches the same kernels every step
     if ws > 1:
         from paper_2502_13245_gb300 import multi
@@ -700,12 +721,13 @@ def main():
     # serving on the same index: single-query requests with radii mixed r / 1.5r / 2r, open-loop Poisson
     serve = None
     if rank == 0 and args.line_serve:
-        batch_qps, srows = serve_rates(args, ds, rr, gi, stream, dev, variant, beam, form[1], form[2],
-                                       [float(x) for x in args.line_serve.split(",") if x], args.line_serve_secs)
+        batch_qps, srows, cost = serve_rates(args, ds, rr, gi, stream, dev, variant, beam, form[1], form[2],
+                                             [float(x) for x in args.line_serve.split(",") if x],
+                                             args.line_serve_secs)
         serve = {"what": "single-query requests, radii drawn from r / 1.5r / 2r, open-loop Poisson arrivals for "
                          "%.1f s per rate, %s b=%d, %d workers, batches up to %d" % (
                              args.line_serve_secs, variant, beam, args.serve_workers, args.serve_max_batch),
-                 "batch_qps_on_this_mix": batch_qps,
+                 "batch_qps_on_this_mix": batch_qps, "mix_cost": cost,
                  "rates": [{"offered_qps": r["offered_qps"], "achieved_qps": r["achieved_qps"],
                             "p50_ms": r["p50_us"] / 1000, "p99_ms": r["p99_us"] / 1000, "canceled": r["canceled"],
                             "mean_batch": r["mean_batch"]} for r in srows]}
@@ -739,6 +761,10 @@ def main():
                     args.precision],
                 "variant": variant, "beam": beam, "ap": best["ap"], "es_vl": form[1], "es_radius_over_r": form[2],
                 "launch_shape": tuned or "library default",
+                "phase_ms": {"beam": float(phase_ms[0]), "phase2": float(phase_ms[1]), "output": float(phase_ms[2]),
+                             "total": float(phase_ms[3]), "phase2_steps": int(prof.phase2_steps),
+                             "phase2_queries": int(prof.phase2_queries),
+                             "what": "per-phase device time of profiled calls of the same form (CUDA events)"},
                 "beam_phase_evals_per_distinct": float(st_beam["evals"].sum()) / max(1, int(st_beam["distinct"].sum())),
                 "plain_beam_form": None if plain_best is None else {
                     "beam": plain_best["beam"], "qps": plain_best["qps"], "ap": plain_best["ap"]},

@@ -329,6 +329,10 @@ CONFIGS = {
     # fall apart, and greedy AP stays at 0.34 at b=128; with L=48 it is 0.9965 (20,000 queries)
     "c3": Config("c3", 10_000_000, 256, 100_000, "u8", M_L2, 5000, 12.0, 20000, 64, 48, 1.2, 2, 3, 2.0,
                  streams=64, builder="gpu"),
+    # the same recipe at 2,000,000 points and 20,000 queries (1 GB of vectors + adjacency, well above L2): the
+    # case that profiler captures of the 10^7-point workload's kernels run on
+    "c3p": Config("c3p", 2_000_000, 256, 20_000, "u8", M_L2, 5000, 12.0, 20000, 64, 48, 1.2, 2, 3, 2.0,
+                  streams=64, builder="gpu"),
 }
 
 
