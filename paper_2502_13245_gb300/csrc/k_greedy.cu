@@ -10,6 +10,18 @@
 // exact bitmap of n bits ("seen": ids already in F or already evaluated), so
 // every point is evaluated at most once per query and enters F at most once.
 // The items of a slot are exactly its result set V.
+//
+// 8-bit indexes run each level as two flat passes instead of one warp per
+// item, so that the dependent chain of an item (its adjacency row, the seen
+// bits of its neighbours, their vectors) is spread over many independent
+// threads: the expand pass gives every (item, neighbour) pair a thread that
+// tests-and-sets the neighbour's seen bit and appends the first-seen ones to
+// a candidate list; the evaluate pass gives each candidate a lane group that
+// gathers its vector and the query's, and appends the in-range ones as items
+// of the next level.  The set of items is the same either way (the bitmap
+// admits each point once per query, whichever pair claims it first).
+#include <algorithm>
+
 #include "rr_common.cuh"
 
 namespace rr {
@@ -168,6 +180,130 @@ rr_status level_t(const GreedyArgs &g, cudaStream_t st) {
     return RR_OK;
 }
 
+// Expand pass: thread per (item, neighbour) of items [begin, end); first-seen neighbours become
+// candidates (slot << 32 | id).  Whole warps run the loop (ballot-aggregated appends).
+template <bool COUNT>
+__global__ void __launch_bounds__(256) greedy_expand_kernel(GreedyArgs g) {
+    const SearchArgs &a = g.s;
+    const int lane = lane_id();
+    const int R = a.R;
+    const int64_t total = (g.end - g.begin) * (int64_t)R;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) & ~(int64_t)31; base < total;
+         base += stride) {
+        const int64_t x = base + lane;
+        bool fresh = false;
+        uint64_t e = 0;
+        int32_t slot = 0;
+        if (x < total) {
+            const int64_t it = g.begin + x / R;
+            const int k = (int)(x % R);
+            slot = g.item_slot[it];
+            const uint32_t p = key_id(g.item_key[it]);
+            const uint32_t j = __ldg(a.adj + (size_t)p * R + k);
+            if (COUNT && k == 0 && a.stats) atomicAdd(&a.stats[g.qlist[slot]].visits_phase2, 1);
+            if (j < (uint32_t)a.n) {
+                uint32_t *w = g.seen + (size_t)slot * g.seen_words + (j >> 5);
+                const uint32_t bit = 1u << (j & 31);
+                // bits only go from 0 to 1 during the phase: a set bit read here is final
+                if (!(*w & bit)) fresh = !(atomicOr(w, bit) & bit);
+                e = ((uint64_t)(uint32_t)slot << 32) | j;
+            }
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, fresh);
+        if (m) {
+            unsigned long long b0 = 0;
+            if (lane == 0) b0 = atomicAdd(g.ccount, (unsigned long long)__popc(m));
+            b0 = __shfl_sync(0xffffffffu, b0, 0);
+            if (fresh) {
+                const unsigned long long pos = b0 + __popc(m & lanemask_lt());
+                if (pos < (unsigned long long)g.ccap) g.cand[pos] = e;
+                else atomicExch(a.error, 7);  // the host sizes the list for the chunk: cannot happen
+            }
+        }
+    }
+}
+
+// Evaluate pass: each lane group of lpv lanes takes UN candidates at a time (their query and point
+// vectors gathered before any is reduced); in-range ones are appended to the item list.
+template <int DT, bool COUNT>
+__global__ void __launch_bounds__(256, 4) greedy_eval_kernel(GreedyArgs g) {
+    constexpr int UN = 4;
+    using T = typename Acc<DT>::T;
+    const SearchArgs &a = g.s;
+    const int lane = lane_id();
+    const int lpv = a.lpv, sub = lane & (lpv - 1), grp = lane / lpv, ngrp = 32 / lpv;
+    const int64_t nc = (int64_t)min(*(volatile unsigned long long *)g.ccount, (unsigned long long)g.ccap);
+    const int64_t warp_g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t per = (int64_t)ngrp * UN;
+    for (int64_t c0 = warp_g * per; c0 < nc; c0 += nwarps * per) {
+        uint4 q[UN], v[UN];
+        int32_t slot[UN], qi[UN];
+        uint32_t id[UN];
+#pragma unroll
+        for (int u = 0; u < UN; u++) {
+            const int64_t c = c0 + grp + (int64_t)ngrp * u;
+            const bool ok = c < nc;
+            const uint64_t e = ok ? g.cand[c] : 0ull;
+            slot[u] = (int32_t)(e >> 32);
+            id[u] = (uint32_t)e;
+            qi[u] = ok ? g.qlist[slot[u]] : 0;
+            const bool ch = ok && sub < a.row_chunks;
+            q[u] = ch ? ldg16(a.queries + (size_t)qi[u] * a.row_stride + (size_t)sub * 16) : make_uint4(0, 0, 0, 0);
+            v[u] = ch ? ldg16(a.vec + (size_t)id[u] * a.row_stride + (size_t)sub * 16) : make_uint4(0, 0, 0, 0);
+        }
+#pragma unroll
+        for (int u = 0; u < UN; u++) {
+            T sum = 0;
+            if (a.metric == MET_L2) Acc<DT>::l2(sum, q[u], v[u]);
+            else Acc<DT>::ip(sum, q[u], v[u]);
+            sum = group_sum(sum, lpv);
+            const int64_t c = c0 + grp + (int64_t)ngrp * u;
+            const uint32_t dk = finish_dk(sum, a.metric);
+            const bool lead = sub == 0 && c < nc;
+            const bool in = lead && dk <= a.rkey[qi[u]];
+            if (COUNT && lead && a.stats) {
+                atomicAdd(&a.stats[qi[u]].evals, 1);
+                if (mark_bit(a.count_bits + (size_t)qi[u] * a.words_per_q, id[u]))
+                    atomicAdd(&a.stats[qi[u]].distinct, 1);
+            }
+            const unsigned m = __ballot_sync(0xffffffffu, in);
+            if (!m) continue;
+            unsigned long long b0 = 0;
+            if (lane == 0) b0 = atomicAdd(g.tail, (unsigned long long)__popc(m));
+            b0 = __shfl_sync(0xffffffffu, b0, 0);
+            if (in) {
+                const unsigned long long pos = b0 + __popc(m & lanemask_lt());
+                if (pos < (unsigned long long)g.cap) {
+                    g.item_key[pos] = make_key(dk, id[u]);
+                    g.item_slot[pos] = slot[u];
+                    atomicAdd(g.slot_count + slot[u], 1);
+                } else {
+                    g.slot_trunc[slot[u]] = 1;
+                }
+            }
+        }
+    }
+}
+
+template <int DT>
+rr_status two_pass_t(const GreedyArgs &g, cudaStream_t st) {
+    const int64_t pairs = (g.end - g.begin) * (int64_t)g.s.R;
+    int64_t blocks = (pairs + 255) / 256;
+    blocks = std::max<int64_t>(1, std::min<int64_t>(blocks, 152 * 32));
+    if (g.s.count_bits) greedy_expand_kernel<true><<<(unsigned)blocks, 256, 0, st>>>(g);
+    else greedy_expand_kernel<false><<<(unsigned)blocks, 256, 0, st>>>(g);
+    RR_CUDA(cudaGetLastError());
+    // the candidate count is read on the device; the grid covers a full level's worth of candidates
+    int64_t eblocks = std::max<int64_t>(1, std::min<int64_t>((pairs + 255) / 256, 152 * 16));
+    if (g.s.count_bits) greedy_eval_kernel<DT, true><<<(unsigned)eblocks, 256, 0, st>>>(g);
+    else greedy_eval_kernel<DT, false><<<(unsigned)eblocks, 256, 0, st>>>(g);
+    RR_CUDA(cudaGetLastError());
+    note_launch(2);
+    return RR_OK;
+}
+
 __global__ void set_counts_kernel(int32_t *res_count, uint8_t *flags, const int32_t *qlist, const int32_t *slot_count,
                                   const int32_t *slot_trunc, int32_t n) {
     for (int32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
@@ -190,18 +326,28 @@ rr_status launch_greedy_init(const GreedyArgs &g, cudaStream_t st, int) {
     return RR_OK;
 }
 
+bool greedy_two_pass(int dtype_code) { return dtype_code == DT_U8 || dtype_code == DT_I8; }
+
 rr_status launch_greedy_level(const GreedyArgs &g, cudaStream_t st, int dtype_code) {
     if (g.end <= g.begin) return RR_OK;
     const int cpl = (g.s.row_chunks + 31) / 32;
     switch (dtype_code) {
-        case DT_U8: return level_t<DT_U8, 1>(g, st);
-        case DT_I8: return level_t<DT_I8, 1>(g, st);
+        case DT_U8:
+            if (g.s.row_chunks > 32 || !g.cand || !g.ccount) break;
+            return two_pass_t<DT_U8>(g, st);
+        case DT_I8:
+            if (g.s.row_chunks > 32 || !g.cand || !g.ccount) break;
+            return two_pass_t<DT_I8>(g, st);
         case DT_F32:
             if (g.s.prec == RR_PREC_BF16) return level_t<DT_BF16, 4>(g, st);
             if (g.s.prec == RR_PREC_FP8) return level_t<DT_FP8, 4>(g, st);
             if (cpl <= 1) return level_t<DT_F32, 1>(g, st);
             if (cpl <= 2) return level_t<DT_F32, 2>(g, st);
             return level_t<DT_F32, 4>(g, st);
+    }
+    if (dtype_code == DT_U8 || dtype_code == DT_I8) {
+        set_error("greedy phase: 8-bit levels need a candidate list and rows of at most 512 bytes");
+        return RR_EINTERNAL;
     }
     set_error("greedy phase: unsupported element type %d", dtype_code);
     return RR_EINVAL;

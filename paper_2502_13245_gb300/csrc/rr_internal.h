@@ -77,6 +77,7 @@ struct rr_index {
     rr::Grow outbuf;        // output staging (sort keys, host-result staging)
     rr::Grow dbl_s[2];      // doubling: S of the active queries (double buffered)
     rr::Grow dbl_tmp;       // doubling: sort scratch of S u V
+    rr::Grow cand;          // greedy candidate list of a level chunk (8-bit indexes)
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};  // profile: start, beam, phase2, end
     rr_profile prof = {};
     // low-precision traversal copies of an fp32 index (built on first use)
@@ -174,10 +175,17 @@ struct GreedyArgs {
     int32_t *slot_count;       // results per slot
     int32_t *slot_trunc;       // 1 if a result of the slot was dropped (capacity)
     int64_t begin, end;        // current level [begin, end)
+    // 8-bit indexes: a level runs as an expand pass and an evaluate pass over a candidate list
+    uint64_t *cand;            // (slot << 32 | id) of the neighbours first seen in this chunk of the level
+    unsigned long long *ccount;  // device: candidates appended (zeroed before each chunk)
+    int64_t ccap;              // candidate capacity (items per chunk x R)
 };
 
 rr_status launch_greedy_init(const GreedyArgs &g, cudaStream_t s, int dtype_code);
 rr_status launch_greedy_level(const GreedyArgs &g, cudaStream_t s, int dtype_code);
+// true when launch_greedy_level runs the two-pass form (expand, then evaluate) for this element type;
+// it then needs g.cand / g.ccount sized for the level's chunk, and processes items [begin, end) of g
+bool greedy_two_pass(int dtype_code);
 
 // One round of Alg. 3 (a BeamSearch with beam b from B = top-b(S)) for the
 // active doubling slots; i indexes the active list, slot = act[i].

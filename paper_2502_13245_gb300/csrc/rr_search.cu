@@ -299,6 +299,8 @@ rr_status run_greedy(Search &S, int32_t np2, GreedyOut &go) {
     *ht = (unsigned long long)init;
     RR_CUDA(cudaMemcpyAsync(g.tail, ht, 8, cudaMemcpyHostToDevice, S.st));
     if ((s = launch_greedy_init(g, S.st, ix->dtype)) != RR_OK) return s;
+    const bool two_pass = greedy_two_pass(ix->dtype) && a.row_chunks <= 32;
+    g.ccount = S.tail + 1;  // the second word of the tail block
     int64_t begin = 0, end = init, levels = 0;
     while (begin < end) {
         const int64_t need = end + (end - begin) * (int64_t)ix->R;
@@ -308,9 +310,23 @@ rr_status run_greedy(Search &S, int32_t np2, GreedyOut &go) {
             if ((s = grow(ix->item_slot, (size_t)ncap * 4, (size_t)end * 4, S.st)) != RR_OK) return s;
             refresh();
         }
-        g.begin = begin;
-        g.end = end;
-        if ((s = launch_greedy_level(g, S.st, ix->dtype)) != RR_OK) return s;
+        // 8-bit indexes: expand + evaluate passes over a candidate list of at most 2^27 entries, so a
+        // long level runs in chunks of items
+        int64_t chunk = end - begin;
+        if (two_pass) {
+            const int64_t want_c = std::max<int64_t>(ix->R, std::min<int64_t>((end - begin) * (int64_t)ix->R,
+                                                                            (int64_t)1 << 27));
+            if ((s = grow(ix->cand, (size_t)want_c * 8, 0, S.st)) != RR_OK) return s;
+            g.cand = (uint64_t *)ix->cand.p;
+            g.ccap = (int64_t)(ix->cand.bytes / 8);
+            chunk = std::max<int64_t>(1, g.ccap / ix->R);
+        }
+        for (int64_t cb = begin; cb < end; cb += chunk) {
+            if (two_pass) RR_CUDA(cudaMemsetAsync(g.ccount, 0, 8, S.st));
+            g.begin = cb;
+            g.end = std::min(end, cb + chunk);
+            if ((s = launch_greedy_level(g, S.st, ix->dtype)) != RR_OK) return s;
+        }
         RR_CUDA(cudaMemcpyAsync(ht, g.tail, 8, cudaMemcpyDeviceToHost, S.st));
         RR_CUDA(cudaStreamSynchronize(S.st));
         begin = end;
