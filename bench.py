@@ -43,9 +43,10 @@ VARIANTS = ["greedy", "greedy_es", "doubling", "doubling_es", "beam", "beam_es"]
 ES_GRID = [(20, 1.0), (50, 1.5), (100, 2.0)]
 AP_TARGET = 0.95
 MULTI_PARENT = (2, 4)
-# DRAM bytes (read + write) of one beam-kernel launch from an ncu capture of the current kernel
-# (profiles/beam_kernel_c1_b192.md), keyed by (workload, variant, b); cleared whenever the kernel changes
-MEASURED_TRAFFIC = {("c1", "greedy", 192): 1.044849e9 + 9.909248e6}
+# DRAM bytes (read + write) of one launch of the roofline's kernel from an ncu capture of the current kernel
+# on this workload, keyed by (workload, variant, b); cleared whenever the kernel changes (none is current:
+# the 10^7-point workload's kernels are captured on its 2M-point recipe, see profiles/)
+MEASURED_TRAFFIC = {}
 
 
 def log(*a):

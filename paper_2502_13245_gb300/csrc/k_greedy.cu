@@ -181,43 +181,62 @@ rr_status level_t(const GreedyArgs &g, cudaStream_t st) {
 }
 
 // Expand pass: thread per (item, neighbour) of items [begin, end); first-seen neighbours become
-// candidates (slot << 32 | id).  Whole warps run the loop (ballot-aggregated appends).
+// candidates {id, slot, query} (16 bytes).  A warp takes 32 x EU consecutive pairs per iteration and each lane
+// issues the loads of its EU pairs together (item, then row entry, then bitmap word), so their
+// latencies overlap.  Whole warps run the loop (ballot-aggregated appends).
 template <bool COUNT>
 __global__ void __launch_bounds__(256) greedy_expand_kernel(GreedyArgs g) {
+    constexpr int EU = 4;
     const SearchArgs &a = g.s;
     const int lane = lane_id();
     const int R = a.R;
     const int64_t total = (g.end - g.begin) * (int64_t)R;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t base = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) & ~(int64_t)31; base < total;
-         base += stride) {
-        const int64_t x = base + lane;
-        bool fresh = false;
-        uint64_t e = 0;
-        int32_t slot = 0;
-        if (x < total) {
-            const int64_t it = g.begin + x / R;
-            const int k = (int)(x % R);
-            slot = g.item_slot[it];
-            const uint32_t p = key_id(g.item_key[it]);
-            const uint32_t j = __ldg(a.adj + (size_t)p * R + k);
-            if (COUNT && k == 0 && a.stats) atomicAdd(&a.stats[g.qlist[slot]].visits_phase2, 1);
-            if (j < (uint32_t)a.n) {
-                uint32_t *w = g.seen + (size_t)slot * g.seen_words + (j >> 5);
-                const uint32_t bit = 1u << (j & 31);
-                // bits only go from 0 to 1 during the phase: a set bit read here is final
-                if (!(*w & bit)) fresh = !(atomicOr(w, bit) & bit);
-                e = ((uint64_t)(uint32_t)slot << 32) | j;
+    const int64_t warp_g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t base = warp_g * 32 * EU; base < total; base += nwarps * 32 * EU) {
+        int32_t slot[EU], qi[EU];
+        uint32_t p[EU], j[EU], w[EU];
+        uint32_t *wp[EU];
+#pragma unroll
+        for (int u = 0; u < EU; u++) {
+            const int64_t x = base + u * 32 + lane;
+            slot[u] = -1;
+            if (x < total) {
+                const int64_t it = g.begin + x / R;
+                slot[u] = g.item_slot[it];
+                p[u] = key_id(g.item_key[it]);
             }
         }
-        const unsigned m = __ballot_sync(0xffffffffu, fresh);
-        if (m) {
+#pragma unroll
+        for (int u = 0; u < EU; u++) {
+            const int64_t x = base + u * 32 + lane;
+            j[u] = slot[u] >= 0 ? __ldg(a.adj + (size_t)p[u] * R + (int)(x % R)) : kSent;
+            qi[u] = slot[u] >= 0 ? g.qlist[slot[u]] : 0;
+            if (COUNT && slot[u] >= 0 && x % R == 0 && a.stats) atomicAdd(&a.stats[qi[u]].visits_phase2, 1);
+        }
+#pragma unroll
+        for (int u = 0; u < EU; u++) {
+            wp[u] = nullptr;
+            w[u] = 0xFFFFFFFFu;
+            if (j[u] < (uint32_t)a.n) {
+                wp[u] = g.seen + (size_t)slot[u] * g.seen_words + (j[u] >> 5);
+                w[u] = *wp[u];  // bits only go from 0 to 1 during the phase: a set bit read here is final
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < EU; u++) {
+            const uint32_t bit = 1u << (j[u] & 31);
+            bool fresh = false;
+            if (wp[u] && !(w[u] & bit)) fresh = !(atomicOr(wp[u], bit) & bit);
+            const unsigned m = __ballot_sync(0xffffffffu, fresh);
+            if (!m) continue;
             unsigned long long b0 = 0;
             if (lane == 0) b0 = atomicAdd(g.ccount, (unsigned long long)__popc(m));
             b0 = __shfl_sync(0xffffffffu, b0, 0);
             if (fresh) {
                 const unsigned long long pos = b0 + __popc(m & lanemask_lt());
-                if (pos < (unsigned long long)g.ccap) g.cand[pos] = e;
+                if (pos < (unsigned long long)g.ccap)
+                    reinterpret_cast<uint4 *>(g.cand)[pos] = make_uint4(j[u], (uint32_t)slot[u], (uint32_t)qi[u], 0u);
                 else atomicExch(a.error, 7);  // the host sizes the list for the chunk: cannot happen
             }
         }
@@ -245,10 +264,10 @@ __global__ void __launch_bounds__(256, 4) greedy_eval_kernel(GreedyArgs g) {
         for (int u = 0; u < UN; u++) {
             const int64_t c = c0 + grp + (int64_t)ngrp * u;
             const bool ok = c < nc;
-            const uint64_t e = ok ? g.cand[c] : 0ull;
-            slot[u] = (int32_t)(e >> 32);
-            id[u] = (uint32_t)e;
-            qi[u] = ok ? g.qlist[slot[u]] : 0;
+            const uint4 e = ok ? reinterpret_cast<const uint4 *>(g.cand)[c] : make_uint4(0u, 0u, 0u, 0u);
+            id[u] = e.x;
+            slot[u] = (int32_t)e.y;
+            qi[u] = (int32_t)e.z;
             const bool ch = ok && sub < a.row_chunks;
             q[u] = ch ? ldg16(a.queries + (size_t)qi[u] * a.row_stride + (size_t)sub * 16) : make_uint4(0, 0, 0, 0);
             v[u] = ch ? ldg16(a.vec + (size_t)id[u] * a.row_stride + (size_t)sub * 16) : make_uint4(0, 0, 0, 0);
@@ -290,8 +309,8 @@ __global__ void __launch_bounds__(256, 4) greedy_eval_kernel(GreedyArgs g) {
 template <int DT>
 rr_status two_pass_t(const GreedyArgs &g, cudaStream_t st) {
     const int64_t pairs = (g.end - g.begin) * (int64_t)g.s.R;
-    int64_t blocks = (pairs + 255) / 256;
-    blocks = std::max<int64_t>(1, std::min<int64_t>(blocks, 152 * 32));
+    int64_t blocks = (pairs + 1023) / 1024;  // 4 pairs per thread and iteration
+    blocks = std::max<int64_t>(1, std::min<int64_t>(blocks, 152 * 16));
     if (g.s.count_bits) greedy_expand_kernel<true><<<(unsigned)blocks, 256, 0, st>>>(g);
     else greedy_expand_kernel<false><<<(unsigned)blocks, 256, 0, st>>>(g);
     RR_CUDA(cudaGetLastError());

@@ -2,6 +2,8 @@
 // of Alg. 6 / Alg. 3 for the whole batch): count -> exclusive scan -> copy or
 // scatter -> per-query sort by (distance, id) -> decode keys into ids and
 // distances.
+#include <algorithm>
+
 #include "rr_common.cuh"
 
 namespace rr {
@@ -173,7 +175,12 @@ rr_status launch_scatter_items(const OutArgs &o, const uint64_t *item_key, const
 rr_status launch_sort_segments(const OutArgs &o, uint64_t *tmp, const int32_t *qlist, int32_t nlist, int64_t,
                                cudaStream_t st) {
     if (nlist <= 0) return RR_OK;
-    const int smem_cap = 16384;  // keys: 128 KB of shared memory
+    // keys: the largest shared-memory block a CTA may take (227 KB), so segments of up to 29,056 results
+    // are sorted on chip; longer ones in place in global memory
+    int dev = 0, optin = 0;
+    RR_CUDA(cudaGetDevice(&dev));
+    RR_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    const int smem_cap = std::max(4096, optin / 8);
     size_t smem = (size_t)smem_cap * 8;
     RR_CUDA(cudaFuncSetAttribute(sort_segments_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int blocks = nlist < 152 * 2 ? nlist : 152 * 2;

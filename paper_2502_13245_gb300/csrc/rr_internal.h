@@ -176,7 +176,8 @@ struct GreedyArgs {
     int32_t *slot_trunc;       // 1 if a result of the slot was dropped (capacity)
     int64_t begin, end;        // current level [begin, end)
     // 8-bit indexes: a level runs as an expand pass and an evaluate pass over a candidate list
-    uint64_t *cand;            // (slot << 32 | id) of the neighbours first seen in this chunk of the level
+    uint64_t *cand;            // {id, slot, query, 0} (16 bytes each) of the neighbours first seen in this
+                               // chunk of the level
     unsigned long long *ccount;  // device: candidates appended (zeroed before each chunk)
     int64_t ccap;              // candidate capacity (items per chunk x R)
 };

@@ -310,15 +310,15 @@ rr_status run_greedy(Search &S, int32_t np2, GreedyOut &go) {
             if ((s = grow(ix->item_slot, (size_t)ncap * 4, (size_t)end * 4, S.st)) != RR_OK) return s;
             refresh();
         }
-        // 8-bit indexes: expand + evaluate passes over a candidate list of at most 2^27 entries, so a
-        // long level runs in chunks of items
+        // 8-bit indexes: expand + evaluate passes over a candidate list of at most 2^27 entries (16 bytes
+        // each), so a long level runs in chunks of items
         int64_t chunk = end - begin;
         if (two_pass) {
             const int64_t want_c = std::max<int64_t>(ix->R, std::min<int64_t>((end - begin) * (int64_t)ix->R,
                                                                             (int64_t)1 << 27));
-            if ((s = grow(ix->cand, (size_t)want_c * 8, 0, S.st)) != RR_OK) return s;
+            if ((s = grow(ix->cand, (size_t)want_c * 16, 0, S.st)) != RR_OK) return s;
             g.cand = (uint64_t *)ix->cand.p;
-            g.ccap = (int64_t)(ix->cand.bytes / 8);
+            g.ccap = (int64_t)(ix->cand.bytes / 16);
             chunk = std::max<int64_t>(1, g.ccap / ix->R);
         }
         for (int64_t cb = begin; cb < end; cb += chunk) {
