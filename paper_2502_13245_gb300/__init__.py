@@ -346,6 +346,11 @@ def rr_beam_search_noalloc(handle, queries, radius, variant, params, out_counts,
     return st
 
 
+def beam_hash_lg(beam: int) -> int:
+    """log2 of the beam kernel's default seen-table size for beam b (what seen_log2 = 0 selects)."""
+    return 10 if beam <= 256 else 11
+
+
 def rr_debug_set(key: str, value: int):
     """Failure-path hooks for tests: "fail_alloc_after" (N-th next device allocation fails; -1 off),
     "beam_iteration_limit" (per-query iteration guard of the beam / doubling kernels; 0 default)."""

@@ -256,7 +256,7 @@ __device__ __forceinline__ void search_query(const SearchArgs &a, int hlg, int64
         if (nc == 0) { cur = nxt; continue; }
         evals += nc;
         if constexpr (LP) {
-            eval_candidates_lp<DT, 8>(a, qf, qn2, cid, nc, ckey);
+            eval_candidates_lp<DT, DT == DT_FP8 ? 4 : 8>(a, qf, qn2, cid, nc, ckey);
         } else if constexpr (CPL == 1 && (DT == DT_U8 || DT == DT_I8)) {
             // few new candidates (late in a search): a shallower unroll wastes fewer lanes (exact integer
             // sums, so the keys do not depend on it)
@@ -488,9 +488,10 @@ rr_status launch_beam(const SearchArgs &a, int wpc, cudaStream_t st, int dtype_c
         case DT_U8: return launch_b<DT_U8, 1>(a, wpc, hlg, st);
         case DT_I8: return launch_b<DT_I8, 1>(a, wpc, hlg, st);
         case DT_F32:
-            // low-precision traversal: CPL = 4 covers the exact rows of every d <= 512
-            if (a.prec == RR_PREC_BF16) return launch_b<DT_BF16, 4>(a, wpc, hlg, st);
-            if (a.prec == RR_PREC_FP8) return launch_b<DT_FP8, 4>(a, wpc, hlg, st);
+            // low-precision traversal: the exact-recheck rows need CPL chunks per lane (2 up to d = 256,
+            // 4 up to d = 512); the smaller instantiation keeps the FP8 kernel out of register spills
+            if (a.prec == RR_PREC_BF16) return cpl <= 2 ? launch_b<DT_BF16, 2>(a, wpc, hlg, st) : launch_b<DT_BF16, 4>(a, wpc, hlg, st);
+            if (a.prec == RR_PREC_FP8) return cpl <= 2 ? launch_b<DT_FP8, 2>(a, wpc, hlg, st) : launch_b<DT_FP8, 4>(a, wpc, hlg, st);
             if (cpl <= 1) return launch_b<DT_F32, 1>(a, wpc, hlg, st);
             if (cpl <= 2) return launch_b<DT_F32, 2>(a, wpc, hlg, st);
             return launch_b<DT_F32, 4>(a, wpc, hlg, st);

@@ -191,7 +191,7 @@ __global__ void __launch_bounds__(128) round_kernel(DoublingRound d) {
         __syncwarp();
         if (nc == 0) continue;
         evals += nc;
-        if constexpr (LP) eval_candidates_lp<DT, 8>(a, qf, qn2, s.cid, nc, s.ckey);
+        if constexpr (LP) eval_candidates_lp<DT, DT == DT_FP8 ? 4 : 8>(a, qf, qn2, s.cid, nc, s.ckey);
         else eval_candidates<DT, CPL, UN>(a, q, s.cid, nc, s.ckey);
         __syncwarp();
         if (cbits) {
@@ -430,8 +430,8 @@ rr_status launch_doubling_round(const DoublingRound &d, cudaStream_t st, int dty
         case DT_U8: return round_t<DT_U8, 1>(d, st);
         case DT_I8: return round_t<DT_I8, 1>(d, st);
         case DT_F32:
-            if (d.s.prec == RR_PREC_BF16) return round_t<DT_BF16, 4>(d, st);
-            if (d.s.prec == RR_PREC_FP8) return round_t<DT_FP8, 4>(d, st);
+            if (d.s.prec == RR_PREC_BF16) return cpl <= 2 ? round_t<DT_BF16, 2>(d, st) : round_t<DT_BF16, 4>(d, st);
+            if (d.s.prec == RR_PREC_FP8) return cpl <= 2 ? round_t<DT_FP8, 2>(d, st) : round_t<DT_FP8, 4>(d, st);
             if (cpl <= 1) return round_t<DT_F32, 1>(d, st);
             if (cpl <= 2) return round_t<DT_F32, 2>(d, st);
             return round_t<DT_F32, 4>(d, st);

@@ -64,16 +64,8 @@ __global__ void __launch_bounds__(256) greedy_level_kernel(GreedyArgs g) {
         const int32_t slot = g.item_slot[it];
         const uint32_t p = key_id(g.item_key[it]);
         const int32_t qi = g.qlist[slot];
-        constexpr bool LP = is_lowp(DT);
         uint4 q[CPL];
-        float qf[16];
-        float qn2 = 0.f;
-        if constexpr (LP) {
-            load_query_lp<DT>(a, reinterpret_cast<const float *>(a.queries + (size_t)qi * a.row_stride), qf);
-            qn2 = query_norm2_lp(a, qf);
-        } else {
-            load_query<CPL>(a, a.queries + (size_t)qi * a.row_stride, q);
-        }
+        load_query<CPL>(a, a.queries + (size_t)qi * a.row_stride, q);
         const uint32_t rk = a.rkey[qi];
         uint32_t *seen = g.seen + (size_t)slot * g.seen_words;
         // f in N_out(p*) \ V, each evaluated once per query (exact bitmap)
@@ -94,31 +86,8 @@ __global__ void __launch_bounds__(256) greedy_level_kernel(GreedyArgs g) {
                 uint32_t *cb = a.count_bits + (size_t)qi * a.words_per_q;
                 for (int c = lane; c < nc; c += 32) dd += mark_bit(cb, cid[c]);
             }
-            int ne = nc;  // candidates whose exact key is in ckey
-            if constexpr (LP) {
-                // approximate distances first; only candidates within r + slack get the exact fp32 check
-                eval_candidates_lp<DT, 8>(a, qf, qn2, cid, nc, ckey);
-                __syncwarp();
-                const uint32_t rks = slack_key(a, rk, qn2);
-                int m = 0;
-                for (int c0 = 0; c0 < nc; c0 += 32) {
-                    const int c = c0 + lane;
-                    const bool keep = c < nc && key_dk(ckey[c]) <= rks;
-                    const uint32_t id = c < nc ? cid[c] : 0u;
-                    const unsigned msk = __ballot_sync(0xffffffffu, keep);
-                    if (keep) cid[m + __popc(msk & lanemask_lt())] = id;  // in place: m <= c0
-                    m += __popc(msk);
-                }
-                __syncwarp();
-                ne = m;
-                if (m > 0) {
-                    uint4 q32[CPL];
-                    load_query<CPL>(a, a.queries + (size_t)qi * a.row_stride, q32);
-                    eval_candidates<DT_F32, CPL, UN>(a, q32, cid, m, ckey);
-                }
-            } else {
-                eval_candidates<DT, CPL, UN>(a, q, cid, nc, ckey);
-            }
+            const int ne = nc;
+            eval_candidates<DT, CPL, UN>(a, q, cid, nc, ckey);
             __syncwarp();
             // if d(f, q) <= r: F <- F u {f}
             int added = 0;
@@ -358,8 +327,9 @@ rr_status launch_greedy_level(const GreedyArgs &g, cudaStream_t st, int dtype_co
             if (g.s.row_chunks > 32 || !g.cand || !g.ccount) break;
             return two_pass_t<DT_I8>(g, st);
         case DT_F32:
-            if (g.s.prec == RR_PREC_BF16) return level_t<DT_BF16, 4>(g, st);
-            if (g.s.prec == RR_PREC_FP8) return level_t<DT_FP8, 4>(g, st);
+            // the precision form too: nearly every candidate of the in-radius expansion is in range, and an
+            // in-range point needs its exact fp32 distance anyway, so a low-precision first pass would only
+            // add bytes; Alg. 2's levels evaluate in exact fp32 whatever the beam phase traversed in
             if (cpl <= 1) return level_t<DT_F32, 1>(g, st);
             if (cpl <= 2) return level_t<DT_F32, 2>(g, st);
             return level_t<DT_F32, 4>(g, st);
