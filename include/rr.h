@@ -60,7 +60,14 @@ typedef enum {
     RR_DOUBLING = 2,
     RR_DOUBLING_ES = 3,
     RR_GREEDY = 4,
-    RR_GREEDY_ES = 5
+    RR_GREEDY_ES = 5,
+    /* warm-restart doubling, a variant of Alg. 3 that is not in the paper: each round continues the
+     * last instead of restarting from B = S with V = {}.  E (every point evaluated, with its distance)
+     * and V are kept across rounds; a round with beam b starts from the b closest points of E and runs
+     * Alg. 1's loop without visiting a point of V again; it stops when |N| < b, else b doubles (capped
+     * by b_max as in Alg. 3).  The first round is Alg. 1 from the start point, as in Alg. 3. */
+    RR_DOUBLING_WARM = 6,
+    RR_DOUBLING_WARM_ES = 7
 } rr_variant;
 
 typedef enum { RR_U8 = 0, RR_I8 = 1, RR_F32 = 2 } rr_dtype;

@@ -21,9 +21,11 @@ from ._build import LIB, build  # noqa: F401
 RR_OK, RR_EINVAL, RR_ENOMEM, RR_ECUDA, RR_EFORMAT, RR_EOVERFLOW, RR_ETIMEOUT, RR_EBUSY, RR_EINTERNAL = range(9)
 STATUS_NAMES = ["RR_OK", "RR_EINVAL", "RR_ENOMEM", "RR_ECUDA", "RR_EFORMAT", "RR_EOVERFLOW", "RR_ETIMEOUT",
                 "RR_EBUSY", "RR_EINTERNAL"]
-RR_BEAM, RR_BEAM_ES, RR_DOUBLING, RR_DOUBLING_ES, RR_GREEDY, RR_GREEDY_ES = range(6)
+RR_BEAM, RR_BEAM_ES, RR_DOUBLING, RR_DOUBLING_ES, RR_GREEDY, RR_GREEDY_ES, RR_DOUBLING_WARM, RR_DOUBLING_WARM_ES = \
+    range(8)
 VARIANTS = {"beam": RR_BEAM, "beam_es": RR_BEAM_ES, "doubling": RR_DOUBLING, "doubling_es": RR_DOUBLING_ES,
-            "greedy": RR_GREEDY, "greedy_es": RR_GREEDY_ES}
+            "greedy": RR_GREEDY, "greedy_es": RR_GREEDY_ES, "doubling_warm": RR_DOUBLING_WARM,
+            "doubling_warm_es": RR_DOUBLING_WARM_ES}
 RR_U8, RR_I8, RR_F32 = 0, 1, 2
 RR_L2, RR_IP = 0, 1
 RR_PREC_EXACT, RR_PREC_BF16, RR_PREC_FP8 = 0, 1, 2

@@ -107,7 +107,10 @@ __global__ void __launch_bounds__(128) round_kernel(DoublingRound d) {
     uint64_t *M = d.bA + (size_t)i * b;
     uint64_t *M2 = d.bB + (size_t)i * b;
     uint64_t *V = d.v + (size_t)i * d.v_cap;
-    uint32_t *seen = d.seen + (size_t)i * d.seen_words;
+    // warm restart: the bitmap of every id this query ever evaluated lives on across rounds (per slot)
+    uint32_t *seen = d.seen + (size_t)(d.warm ? slot : i) * d.seen_words;
+    uint64_t *EV = d.warm ? d.ev + (size_t)i * d.ev_cap : nullptr;
+    int nev = 0;
     uint32_t *cbits = a.count_bits ? a.count_bits + (size_t)qi * a.words_per_q : nullptr;
     int evals = 0, distinct = 0;
 
@@ -120,9 +123,17 @@ __global__ void __launch_bounds__(128) round_kernel(DoublingRound d) {
         if (lane == 0) {
             M[0] = make_key(dk0, a.start);
             mark_bit(seen, a.start);
+            if (EV) EV[0] = make_key(dk0, a.start);
         }
+        nev = EV ? 1 : 0;
         nM = 1;
         evals = 1;
+    } else if (d.warm) {
+        // B <- the b closest points of E, visited ones still marked (they are not visited again); every id
+        // of E is in seen already: one outside these b can never enter the beam of this round
+        nM = min(b, d.s_cnt[i]);
+        const uint64_t *S = d.s_old + (size_t)i * d.s_cap;
+        for (int t = lane; t < nM; t += 32) M[t] = S[t];
     } else {
         nM = min(b, d.s_cnt[i]);
         const uint64_t *S = d.s_old + (size_t)i * d.s_cap;
@@ -194,6 +205,12 @@ __global__ void __launch_bounds__(128) round_kernel(DoublingRound d) {
         if constexpr (LP) eval_candidates_lp<DT, DT == DT_FP8 ? 4 : 8>(a, qf, qn2, s.cid, nc, s.ckey);
         else eval_candidates<DT, CPL, UN>(a, q, s.cid, nc, s.ckey);
         __syncwarp();
+        if (EV) {
+            // E <- E u the new evaluations (kept for the rounds after this one)
+            if (nev + nc > d.ev_cap) { overflow = true; break; }
+            for (int c = lane; c < nc; c += 32) EV[nev + c] = s.ckey[c];
+            nev += nc;
+        }
         if (cbits) {
             int dd = 0;
             for (int c = lane; c < nc; c += 32) dd += mark_bit(cbits, s.cid[c]);
@@ -323,6 +340,7 @@ __global__ void __launch_bounds__(128) round_kernel(DoublingRound d) {
     if (lane == 0) {
         d.status[i] = cont ? 1 : 0;
         d.nv[i] = nvis;
+        if (d.nev) d.nev[i] = nev;
         if (a.stats) {
             rr_query_stats *st = a.stats + qi;
             if (d.first) {
@@ -349,12 +367,18 @@ __global__ void __launch_bounds__(1024) supdate_kernel(DoublingSUpdate u, int sm
     for (int j = blockIdx.x; j < u.nc; j += gridDim.x) {
         const int i = u.cont[j];
         const int ns = u.first ? 0 : u.s_cnt_old[i];
+        const int ne = u.warm ? u.nev[i] : 0;
         const int nv = u.nv[i];
-        const int m = ns + nv;
-        uint64_t *a = m <= smem_cap ? sk : u.tmp + (size_t)j * (u.s_cap_old + u.v_cap);
+        const int m = ns + ne + nv;
+        uint64_t *a = m <= smem_cap ? sk : u.tmp + (size_t)j * (u.s_cap_old + (u.warm ? u.ev_cap : 0) + u.v_cap);
         const uint64_t *S = u.s_old + (size_t)i * u.s_cap_old;
+        const uint64_t *EV = u.warm ? u.ev + (size_t)i * u.ev_cap : nullptr;
         const uint64_t *V = u.v + (size_t)i * u.v_cap;
-        for (int t = threadIdx.x; t < m; t += blockDim.x) a[t] = (t < ns ? S[t] : V[t - ns]) & ~1ull;
+        for (int t = threadIdx.x; t < m; t += blockDim.x) {
+            if (!u.warm) a[t] = (t < ns ? S[t] : V[t - ns]) & ~1ull;
+            // warm restart: E's keys keep their visited bits, this round's visits get theirs
+            else a[t] = t < ns ? S[t] : (t < ns + ne ? EV[t - ns] & ~1ull : V[t - ns - ne] | 1ull);
+        }
         __syncthreads();
         // bitonic sort with flip stages (min to the lower index; virtual +inf padding)
         int P = 1;
@@ -380,12 +404,15 @@ __global__ void __launch_bounds__(1024) supdate_kernel(DoublingSUpdate u, int sm
                 __syncthreads();
             }
         }
-        // drop repeated keys (S and V share ids), keep the first s_cap_new distinct ones
+        // drop repeated keys (S and V share ids), keep the first s_cap_new distinct ones; warm restart: of the
+        // copies of a key (with and without the visited bit) keep the last, which carries the bit if any does
         uint64_t *out = u.s_new + (size_t)j * u.s_cap_new;
         int carry = 0;
         for (int b0 = 0; b0 < m; b0 += blockDim.x) {
             int t = b0 + threadIdx.x;
-            int keep = (t < m && (t == 0 || a[t] != a[t - 1])) ? 1 : 0;
+            int keep;
+            if (!u.warm) keep = (t < m && (t == 0 || a[t] != a[t - 1])) ? 1 : 0;
+            else keep = (t < m && (t == m - 1 || (a[t] | 1ull) != (a[t + 1] | 1ull))) ? 1 : 0;
             unsigned bm = __ballot_sync(0xffffffffu, keep);
             int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
             int pre = __popc(bm & ((1u << lane) - 1));

@@ -78,6 +78,7 @@ struct rr_index {
     rr::Grow dbl_s[2];      // doubling: S of the active queries (double buffered)
     rr::Grow dbl_tmp;       // doubling: sort scratch of S u V
     rr::Grow cand;          // greedy candidate list of a level chunk (8-bit indexes)
+    rr::Grow dbl_seen;      // warm-restart doubling: per-query bitmaps of every id evaluated
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};  // profile: start, beam, phase2, end
     rr_profile prof = {};
     // low-precision traversal copies of an fp32 index (built on first use)
@@ -213,6 +214,13 @@ struct DoublingRound {
     int64_t cap;
     int32_t *slot_count;      // per slot: final |N|
     int32_t *slot_trunc;      // per slot: 1 if b_max or a capacity cut the search
+    // warm restart (a variant of Alg. 3): s_old holds E, the closest keys evaluated so far with their
+    // visited bits (kept as they are); seen is indexed by slot and kept across rounds (every id ever
+    // evaluated); the round appends every key it evaluates to ev (ev_cap per i, counts in nev)
+    int32_t warm;
+    uint64_t *ev;
+    int64_t ev_cap;
+    int32_t *nev;
 };
 
 // S <- S u V for the continuing slots, truncated to the b_max smallest keys
@@ -232,6 +240,12 @@ struct DoublingSUpdate {
     int64_t s_cap_new;
     uint64_t *tmp;            // j x (s_cap_old + v_cap): sort scratch for long lists
     int32_t first;            // S_old = {start} (its key is V[0] of round 1)
+    // warm restart: E_new <- the s_cap_new closest of E_old u ev, with the visited bit of every key of V set
+    // (tmp then holds j x (s_cap_old + ev_cap + v_cap))
+    int32_t warm;
+    const uint64_t *ev;
+    const int32_t *nev;
+    int64_t ev_cap;
 };
 
 rr_status launch_doubling_round(const DoublingRound &d, cudaStream_t s, int dtype_code);

@@ -301,6 +301,7 @@ rr_status rr_free_index(rr_index *ix) {
     grow_free(ix->dbl_s[1]);
     grow_free(ix->dbl_tmp);
     grow_free(ix->cand);
+    grow_free(ix->dbl_seen);
     for (int k = 0; k < 4; k++)
         if (ix->ev[k]) cudaEventDestroy(ix->ev[k]);
     if (ix->lp_bf16) cudaFree(ix->lp_bf16);
@@ -318,7 +319,7 @@ rr_status rr_index_info_get(const rr_index *ix, rr_index_info *info) {
     info->device = ix->device;
     info->scratch_bytes = (int64_t)ix->arena.cap + (int64_t)ix->phase2.bytes + (int64_t)ix->item_key.bytes +
                           (int64_t)ix->item_slot.bytes + (int64_t)ix->outbuf.bytes + (int64_t)ix->dbl_s[0].bytes +
-                          (int64_t)ix->dbl_s[1].bytes + (int64_t)ix->dbl_tmp.bytes + (int64_t)ix->cand.bytes +
+                          (int64_t)ix->dbl_s[1].bytes + (int64_t)ix->dbl_tmp.bytes + (int64_t)ix->cand.bytes + (int64_t)ix->dbl_seen.bytes +
                           (int64_t)ix->pinned.cap;
     return RR_OK;
 }

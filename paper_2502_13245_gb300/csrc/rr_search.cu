@@ -342,13 +342,18 @@ rr_status run_greedy(Search &S, int32_t np2, GreedyOut &go) {
 }
 
 // Alg. 3 for the np2 queued queries: host-driven rounds over the still active ones.
-rr_status run_doubling(Search &S, int32_t np2, GreedyOut &go) {
+rr_status run_doubling(Search &S, int32_t np2, GreedyOut &go, bool warm) {
     rr_index *ix = S.ix;
     const SearchArgs &a = S.a;
     const int64_t words = (ix->n + 31) / 32;
     const int b_max = S.P.b_max;
     rr_status s;
     go.slot_cursor = S.slot_cursor;
+    if (warm) {
+        // warm restart: one bitmap per query of every id it has evaluated, kept across the rounds
+        if ((s = grow(ix->dbl_seen, ru((size_t)np2 * words * 4), 0, S.st)) != RR_OK) return s;
+        if ((s = launch_zero_words((uint32_t *)ix->dbl_seen.p, (int64_t)np2 * words, S.st)) != RR_OK) return s;
+    }
     RR_CUDA(cudaMemsetAsync(S.slot_cursor, 0, (size_t)np2 * 4, S.st));
     RR_CUDA(cudaMemsetAsync(S.slot_trunc, 0, (size_t)np2 * 4, S.st));
     RR_CUDA(cudaMemsetAsync(S.tail, 0, 8, S.st));
@@ -366,14 +371,18 @@ rr_status run_doubling(Search &S, int32_t np2, GreedyOut &go) {
         S.phase2_steps++;
         const int32_t na = (int32_t)act.size();
         const int64_t v_cap = 4 * (int64_t)b + 1024;
+        // warm restart: every key the round evaluates is kept (at most R per visit)
+        const int64_t ev_cap = warm ? v_cap * ix->R : 0;
         const bool last = (int64_t)b * 2 > b_max;
-        // round scratch in phase2: act | status | nv | beam A | beam B | V | seen
+        // round scratch in phase2: act | status | nv | beam A | beam B | V | seen (| ev | nev)
         size_t off_status = ru((size_t)na * 4), off_nv = off_status + ru((size_t)na * 4);
         size_t off_bA = off_nv + ru((size_t)na * 4);
         size_t off_bB = off_bA + ru((size_t)na * b * 8);
         size_t off_v = off_bB + ru((size_t)na * b * 8);
         size_t off_seen = off_v + ru((size_t)na * v_cap * 8);
-        size_t total = off_seen + ru((size_t)na * words * 4);
+        size_t off_ev = off_seen + (warm ? 0 : ru((size_t)na * words * 4));
+        size_t off_nev = off_ev + ru((size_t)na * ev_cap * 8);
+        size_t total = off_nev + ru((size_t)na * 4);
         if ((s = grow(ix->phase2, total, 0, S.st)) != RR_OK) return s;
         uint8_t *base = (uint8_t *)ix->phase2.p;
         int32_t *act_d = (int32_t *)base;
@@ -383,7 +392,8 @@ rr_status run_doubling(Search &S, int32_t np2, GreedyOut &go) {
         RR_CUDA(cudaStreamSynchronize(S.st));
         memcpy(hs, act.data(), (size_t)na * 4);
         RR_CUDA(cudaMemcpyAsync(act_d, hs, (size_t)na * 4, cudaMemcpyHostToDevice, S.st));
-        if ((s = launch_zero_words((uint32_t *)(base + off_seen), (int64_t)na * words, S.st)) != RR_OK) return s;
+        if (!warm && (s = launch_zero_words((uint32_t *)(base + off_seen), (int64_t)na * words, S.st)) != RR_OK)
+            return s;
         // room for every active query to finish with a full beam this round
         int64_t need = (int64_t)tail_h + (int64_t)na * b;
         if (need > cap && cap < cap_limit) {
@@ -409,8 +419,12 @@ rr_status run_doubling(Search &S, int32_t np2, GreedyOut &go) {
         d.v = (uint64_t *)(base + off_v);
         d.v_cap = v_cap;
         d.nv = (int32_t *)(base + off_nv);
-        d.seen = (uint32_t *)(base + off_seen);
+        d.seen = warm ? (uint32_t *)ix->dbl_seen.p : (uint32_t *)(base + off_seen);
         d.seen_words = words;
+        d.warm = warm ? 1 : 0;
+        d.ev = warm ? (uint64_t *)(base + off_ev) : nullptr;
+        d.ev_cap = ev_cap;
+        d.nev = warm ? (int32_t *)(base + off_nev) : nullptr;
         d.status = (int32_t *)(base + off_status);
         d.item_key = (uint64_t *)ix->item_key.p;
         d.item_slot = (int32_t *)ix->item_slot.p;
@@ -430,11 +444,11 @@ rr_status run_doubling(Search &S, int32_t np2, GreedyOut &go) {
         if (cont.empty()) break;
         // S <- S u V for the continuing queries, into the other buffer
         const int32_t nc = (int32_t)cont.size();
-        const int64_t s_cap_new = std::min<int64_t>(b_max, (first ? 0 : s_cap) + v_cap);
+        const int64_t s_cap_new = std::min<int64_t>(b_max, (first ? 0 : s_cap) + ev_cap + v_cap);
         const int nxt = cur ^ 1;
         size_t sbytes = ru((size_t)nc * s_cap_new * 8) + ru((size_t)nc * 4) + ru((size_t)nc * 4);
         if ((s = grow(ix->dbl_s[nxt], sbytes, 0, S.st)) != RR_OK) return s;
-        const int64_t tmp_row = (first ? 0 : s_cap) + v_cap;
+        const int64_t tmp_row = (first ? 0 : s_cap) + ev_cap + v_cap;
         if ((s = grow(ix->dbl_tmp, (size_t)nc * tmp_row * 8 + 256, 0, S.st)) != RR_OK) return s;
         uint8_t *sb = (uint8_t *)ix->dbl_s[nxt].p;
         int32_t *cnt_new = (int32_t *)(sb + ru((size_t)nc * s_cap_new * 8));
@@ -456,6 +470,10 @@ rr_status run_doubling(Search &S, int32_t np2, GreedyOut &go) {
         u.s_cap_new = s_cap_new;
         u.tmp = (uint64_t *)ix->dbl_tmp.p;
         u.first = first ? 1 : 0;
+        u.warm = warm ? 1 : 0;
+        u.ev = d.ev;
+        u.nev = d.nev;
+        u.ev_cap = ev_cap;
         if ((s = launch_doubling_supdate(u, S.st)) != RR_OK) return s;
         RR_CUDA(cudaStreamSynchronize(S.st));  // hs is reused by the next round
         cur = nxt;
@@ -479,7 +497,7 @@ extern "C" rr_status rr_range_search(rr_index *ix, const void *queries, int64_t 
     if (!ix) { set_error("rr_range_search: index is NULL"); return RR_EINVAL; }
     if (nq < 0 || (nq > 0 && !queries)) { set_error("rr_range_search: bad queries"); return RR_EINVAL; }
     if (nq >= ((int64_t)1 << 31)) { set_error("rr_range_search: nq too large"); return RR_EINVAL; }
-    if (variant < RR_BEAM || variant > RR_GREEDY_ES) { set_error("rr_range_search: bad variant %d", variant); return RR_EINVAL; }
+    if (variant < RR_BEAM || variant > RR_DOUBLING_WARM_ES) { set_error("rr_range_search: bad variant %d", variant); return RR_EINVAL; }
     Search S;
     S.ix = ix;
     S.st = (cudaStream_t)stream;
@@ -491,9 +509,11 @@ extern "C" rr_status rr_range_search(rr_index *ix, const void *queries, int64_t 
     if (P.beam < 1 || P.beam > 512) { set_error("rr_range_search: beam=%d out of [1, 512]", P.beam); return RR_EINVAL; }
     if (P.max_results_total <= 0) P.max_results_total = (int64_t)1 << 28;
     if (P.es_visit_limit < 0) { set_error("rr_range_search: es_visit_limit < 0"); return RR_EINVAL; }
-    const bool doubling = variant == RR_DOUBLING || variant == RR_DOUBLING_ES;
+    const bool warm = variant == RR_DOUBLING_WARM || variant == RR_DOUBLING_WARM_ES;
+    const bool doubling = variant == RR_DOUBLING || variant == RR_DOUBLING_ES || warm;
     const bool greedy = variant == RR_GREEDY || variant == RR_GREEDY_ES;
-    const bool use_es = variant == RR_BEAM_ES || variant == RR_DOUBLING_ES || variant == RR_GREEDY_ES;
+    const bool use_es = variant == RR_BEAM_ES || variant == RR_DOUBLING_ES || variant == RR_GREEDY_ES ||
+                        variant == RR_DOUBLING_WARM_ES;
     if (P.es_metric < RR_ES_VISITED || P.es_metric > RR_ES_TOP10_RATIO) {
         set_error("rr_range_search: unknown early-stopping metric %d", P.es_metric);
         return RR_EINVAL;
@@ -571,7 +591,7 @@ extern "C" rr_status rr_range_search(rr_index *ix, const void *queries, int64_t 
         if ((s = run_greedy(S, np2, go)) != RR_OK) return S.fail(s);
     }
     if (doubling && np2 > 0) {
-        if ((s = run_doubling(S, np2, go)) != RR_OK) return S.fail(s);
+        if ((s = run_doubling(S, np2, go, warm)) != RR_OK) return S.fail(s);
     }
     if (prof) RR_CUDA(cudaEventRecord(ix->ev[2], S.st));
     int64_t total = 0;

@@ -464,7 +464,7 @@ rr_status rr_serve_create(rr_index *ix, const rr_serve_cfg *cfg, rr_server **out
     rr_serve_cfg C;
     if (cfg) C = *cfg; else rr_serve_cfg_init(&C);
     if (C.workers < 1 || C.workers > 64 || C.max_batch < 1 || C.batch_wait_us < 0 || C.result_budget_bytes <= 0 ||
-        C.reserve_per_request < 0 || C.variant < RR_BEAM || C.variant > RR_GREEDY_ES || C.params.beam < 1 ||
+        C.reserve_per_request < 0 || C.variant < RR_BEAM || C.variant > RR_DOUBLING_WARM_ES || C.params.beam < 1 ||
         (C.result_on_device != 0 && C.result_on_device != 1)) {
         set_error("rr_serve_create: invalid configuration");
         return RR_EINVAL;

@@ -52,7 +52,8 @@ def test_c1_brute_force_sample(env):
 
 @pytest.mark.parametrize("variant,beam,k_heavy,k_rand,expand", [("greedy_es", 16, 20, 80, 1), ("greedy", 64, 10, 40, 1),
                                                                  ("beam_es", 64, 5, 95, 1), ("doubling_es", 16, 6, 34, 1),
-                                                                 ("greedy", 64, 10, 40, 2)])
+                                                                 ("greedy", 64, 10, 40, 2),
+                                                                 ("doubling_warm_es", 16, 6, 34, 1)])
 def test_c1_sampled_bit_exact(env, variant, beam, k_heavy, k_rand, expand):
     rr, ds, gi, oi, Qd, gt = env
     res = gi.range_search(Qd, ds.radius, variant, beam=beam, expand=expand)

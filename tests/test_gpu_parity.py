@@ -315,3 +315,30 @@ def test_multi_parent_arguments_are_checked(rr, c0, c0_index):
         c0_index.range_search(c0.Q[:4], c0.radius, "doubling", beam=16, expand=2)
     with pytest.raises(rr.RRError):
         c0_index.range_search(c0.Q[:4], c0.radius, "greedy", beam=16, expand=5)
+
+
+@pytest.mark.parametrize("variant", ["doubling_warm", "doubling_warm_es"])
+@pytest.mark.parametrize("beam", [4, 16])
+def test_c0_warm_doubling_bit_exact(rr, c0, c0_index, c0_oracle, variant, beam):
+    """Warm-restart doubling (a variant of Alg. 3 not in the paper: rounds continue from the kept
+    evaluations and visits) against the oracle's transcription of it: ids, distances, flags and exact
+    counters (every point is evaluated once, so evaluations equal distinct ids)."""
+    o_ids, o_d, o_st = oracle.range_search(c0_oracle, c0.Q, c0.radius, variant, beam=beam, b_max=4096,
+                                           threads=os.cpu_count() or 4)
+    res = c0_index.range_search(c0.Q, c0.radius, variant, beam=beam, b_max=4096, collect_stats=1)
+    assert res.status == rr.RR_OK
+    assert_same(res, o_ids, o_d, len(c0.Q))
+    es = np.array([s["early_stopped"] for s in o_st], bool)
+    assert np.array_equal((res.flags & rr.RR_FLAG_EARLY_STOPPED) != 0, es)
+    ph = np.array([s["phase"] != 0 for s in o_st], bool)
+    assert np.array_equal((res.flags & rr.RR_FLAG_PHASE2) != 0, ph)
+    tr = np.array([s["truncated"] for s in o_st], bool)
+    assert np.array_equal((res.flags & rr.RR_FLAG_TRUNCATED) != 0, tr)
+    assert np.array_equal(res.stats["visits_beam"], [s["visits_beam"] for s in o_st])
+    assert np.array_equal(res.stats["rounds"], [s["rounds"] for s in o_st])
+    assert np.array_equal(res.stats["final_beam"], [s["final_beam"] for s in o_st])
+    assert np.array_equal(res.stats["distinct"], [s["distinct"] for s in o_st])
+    # and it visits no more than the literal Alg. 3 at the same b
+    lit = c0_index.range_search(c0.Q, c0.radius, variant.replace("_warm", ""), beam=beam, b_max=4096,
+                                collect_stats=1)
+    assert res.stats["visits_beam"].sum() <= lit.stats["visits_beam"].sum()
