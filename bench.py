@@ -599,9 +599,10 @@ def main():
             if rank == 0:
                 log("sweep %-12s vl=%-3d esr=%.2fr x%d b=%-4d AP=%.4f  %.3f ms  %.0f QPS" % (
                     form[0], form[1], form[2], form[3] if len(form) > 3 else 1, beam, apv, ms, nq / (ms / 1000)))
+            dbl = form[0].startswith("doubling")
             if apv >= AP_TARGET:
                 reached += 1
-                if reached >= 2:
+                if reached >= (1 if dbl else 2):
                     break  # larger beams only cost more once the target is met
             if form[0].endswith("_es") and abs(apv - last_ap) < 1e-4 and apv < AP_TARGET and beam >= 64:
                 break  # early stop caps this form's precision: more beam does not help
@@ -609,8 +610,10 @@ def main():
                 break  # a form this slow cannot be the fastest one at the target
             best_ok = max([x["qps"] for x in sweep if x["ap"] >= AP_TARGET and x["expand"] == sweep[-1]["expand"]],
                           default=0.0)
-            if nq / (ms / 1000) < best_ok:
-                break  # QPS falls as b grows: this form cannot overtake the fastest one at the target
+            if nq / (ms / 1000) < best_ok and not dbl:
+                # QPS falls as b grows: this form cannot overtake the fastest one at the target (the doubling
+                # forms run on to their own operating point, which the line reports beside the headline)
+                break
             last_ap = apv
     literal = [s for s in sweep if s["expand"] == 1 and not s["variant"].startswith("doubling_warm")]
     ok = [s for s in literal if s["ap"] >= AP_TARGET]

@@ -151,6 +151,11 @@ def range_search(idx: Index, Q, r, variant="greedy_es", beam=64, b_max=32768, es
     Q = np.ascontiguousarray(Q, dtype=idx.X.dtype)
     nq = Q.shape[0]
     radii = np.ascontiguousarray(np.broadcast_to(np.asarray(r, dtype=np.float64), (nq,)))
+    if es_radius is not None and np.ndim(es_radius) == 0 and np.any(float(es_radius) != radii):
+        # one esr for the whole batch: the C batch driver takes it from params (Alg. 6's parallel for)
+        v = VARIANTS[variant] if isinstance(variant, str) else int(variant)
+        p = _Params(v, beam, b_max, es_vl, float(es_radius), ES_METRICS[es_metric], expand)
+        return _batch(idx, Q, radii, p, threads)
     if es_radius is not None and np.any(np.asarray(es_radius) != radii):
         # per-call esr differs from r: fall back to one call per query
         ids, ds, sts = [], [], []
@@ -165,30 +170,36 @@ def range_search(idx: Index, Q, r, variant="greedy_es", beam=64, b_max=32768, es
     out_ids, out_d, out_s = [None] * nq, [None] * nq, [None] * nq
     for rv in np.unique(radii):
         sel = np.nonzero(radii == rv)[0]
-        Qs = np.ascontiguousarray(Q[sel])
-        rs = np.ascontiguousarray(radii[sel])
         p.es_radius = float(rv)
-        m = len(sel)
-        counts = np.zeros(m, np.int64)
-        pid = (ctypes.c_void_p * m)()
-        pd = (ctypes.c_void_p * m)()
-        stats = (Stats * m)()
-        rc = _L().or_range_search_batch(ctypes.byref(idx._s), Qs.ctypes.data, m, rs.ctypes.data, ctypes.byref(p),
-                                        int(threads), counts.ctypes.data, pid, pd, stats)
-        for k in range(m):
-            c = int(counts[k])
-            i = int(sel[k])
-            if c > 0:
-                out_ids[i] = np.ctypeslib.as_array(ctypes.cast(pid[k], ctypes.POINTER(ctypes.c_uint32)), (c,)).copy()
-                out_d[i] = np.ctypeslib.as_array(ctypes.cast(pd[k], ctypes.POINTER(ctypes.c_double)), (c,)).copy()
-            else:
-                out_ids[i] = np.zeros(0, np.uint32)
-                out_d[i] = np.zeros(0, np.float64)
-            out_s[i] = stats[k].as_dict()
-            _L().or_free(pid[k])
-            _L().or_free(pd[k])
-        if rc != 0:
-            raise MemoryError("oracle allocation failed")
+        a, b, c = _batch(idx, np.ascontiguousarray(Q[sel]), np.ascontiguousarray(radii[sel]), p, threads)
+        for k, i in enumerate(sel):
+            out_ids[i], out_d[i], out_s[i] = a[k], b[k], c[k]
+    return out_ids, out_d, out_s
+
+
+def _batch(idx: Index, Qs, rs, p, threads):
+    """or_range_search_batch over queries Qs with radii rs and the given params (marshalling only)."""
+    m = Qs.shape[0]
+    counts = np.zeros(m, np.int64)
+    pid = (ctypes.c_void_p * m)()
+    pd = (ctypes.c_void_p * m)()
+    stats = (Stats * m)()
+    rc = _L().or_range_search_batch(ctypes.byref(idx._s), Qs.ctypes.data, m, rs.ctypes.data, ctypes.byref(p),
+                                    int(threads), counts.ctypes.data, pid, pd, stats)
+    out_ids, out_d, out_s = [], [], []
+    for k in range(m):
+        c = int(counts[k])
+        if c > 0:
+            out_ids.append(np.ctypeslib.as_array(ctypes.cast(pid[k], ctypes.POINTER(ctypes.c_uint32)), (c,)).copy())
+            out_d.append(np.ctypeslib.as_array(ctypes.cast(pd[k], ctypes.POINTER(ctypes.c_double)), (c,)).copy())
+        else:
+            out_ids.append(np.zeros(0, np.uint32))
+            out_d.append(np.zeros(0, np.float64))
+        out_s.append(stats[k].as_dict())
+        _L().or_free(pid[k])
+        _L().or_free(pd[k])
+    if rc != 0:
+        raise MemoryError("oracle allocation failed")
     return out_ids, out_d, out_s
 
 

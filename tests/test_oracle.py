@@ -488,3 +488,14 @@ def test_warm_doubling_evaluates_each_point_once(small):
     _, _, st_l = oracle.range_search(idx, ds.Q, ds.radius, "doubling_warm", beam=8, b_max=4096)
     for st in st_l:
         assert st["evals"] == st["distinct"]
+
+
+def test_batch_with_one_early_stop_radius_matches_single_queries(small):
+    """A constant esr different from r goes through the batch driver; it must agree with the
+    one-query entry point called per query (the binding only marshals)."""
+    ds, idx = small
+    esr = 1.5 * ds.radius
+    a = oracle.range_search(idx, ds.Q[:30], ds.radius, "greedy_es", beam=8, es_vl=5, es_radius=esr, threads=4)
+    for i in range(30):
+        ids, d, st = oracle.range_search_one(idx, ds.Q[i], ds.radius, "greedy_es", beam=8, es_vl=5, es_radius=esr)
+        assert np.array_equal(a[0][i], ids) and np.array_equal(a[1][i], d) and a[2][i] == st
