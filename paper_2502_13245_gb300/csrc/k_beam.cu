@@ -260,7 +260,7 @@ __device__ __forceinline__ void search_query(const SearchArgs &a, int hlg, int64
         } else if constexpr (CPL == 1 && (DT == DT_U8 || DT == DT_I8)) {
             // few new candidates (late in a search): a shallower unroll wastes fewer lanes (exact integer
             // sums, so the keys do not depend on it)
-            const int ngrp = 32 / a.lpv;
+            const int ngrp = 32 >> (__ffs(a.lpv) - 1);
             if (nc <= 2 * ngrp) eval_candidates<DT, CPL, 2>(a, q, cid, nc, ckey);
             else if (nc <= 4 * ngrp) eval_candidates<DT, CPL, 4>(a, q, cid, nc, ckey);
             else eval_candidates<DT, CPL, UN>(a, q, cid, nc, ckey);

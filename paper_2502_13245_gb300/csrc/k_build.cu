@@ -282,17 +282,11 @@ __device__ void warp_sort_u32(uint32_t *v, int m) {
     while (P < m) P <<= 1;
     for (int k = 2; k <= P; k <<= 1) {
         for (int j = k >> 1; j > 0; j >>= 1) {
+            const int lj = __ffs(j) - 1;  // powers of two: shifts and masks
             for (int i = lane; i < P / 2; i += 32) {
-                int lo, hi;
-                if (j == (k >> 1)) {
-                    const int blk = i / (k >> 1), off = i % (k >> 1);
-                    lo = blk * k + off;
-                    hi = blk * k + (k - 1 - off);
-                } else {
-                    const int blk = i / j, off = i % j;
-                    lo = blk * 2 * j + off;
-                    hi = lo + j;
-                }
+                const int off = i & (j - 1);
+                const int lo = ((i >> lj) << (lj + 1)) + off;
+                const int hi = (j == (k >> 1)) ? lo - off + (k - 1 - off) : lo + j;
                 if (hi < m) {
                     const uint32_t x = v[lo], y = v[hi];
                     if (y < x) {

@@ -385,17 +385,11 @@ __global__ void __launch_bounds__(1024) supdate_kernel(DoublingSUpdate u, int sm
         while (P < m) P <<= 1;
         for (int k = 2; k <= P; k <<= 1) {
             for (int jj = k >> 1; jj > 0; jj >>= 1) {
+                const int lj = __ffs(jj) - 1;  // powers of two: shifts and masks
                 for (int t = threadIdx.x; t < P / 2; t += blockDim.x) {
-                    int lo, hi;
-                    if (jj == (k >> 1)) {
-                        int blk = t / (k >> 1), off = t % (k >> 1);
-                        lo = blk * k + off;
-                        hi = blk * k + (k - 1 - off);
-                    } else {
-                        int blk = t / jj, off = t % jj;
-                        lo = blk * 2 * jj + off;
-                        hi = lo + jj;
-                    }
+                    const int off = t & (jj - 1);
+                    const int lo = ((t >> lj) << (lj + 1)) + off;
+                    const int hi = (jj == (k >> 1)) ? lo - off + (k - 1 - off) : lo + jj;
                     if (hi < m) {
                         uint64_t x = a[lo], y = a[hi];
                         if (y < x) { a[lo] = y; a[hi] = x; }

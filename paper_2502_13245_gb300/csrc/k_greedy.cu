@@ -158,30 +158,33 @@ __global__ void __launch_bounds__(256) greedy_expand_kernel(GreedyArgs g) {
     constexpr int EU = 4;
     const SearchArgs &a = g.s;
     const int lane = lane_id();
-    const int R = a.R;
-    const int64_t total = (g.end - g.begin) * (int64_t)R;
-    const int64_t warp_g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t base = warp_g * 32 * EU; base < total; base += nwarps * 32 * EU) {
+    const uint32_t R = (uint32_t)a.R;
+    // pair index in 32 bits: the host splits a level into chunks of at most 2^27 candidates (pairs)
+    const uint32_t total = (uint32_t)((g.end - g.begin) * (int64_t)R);
+    const uint32_t warp_g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t base = warp_g * 32 * EU; base < total; base += nwarps * 32 * EU) {
         int32_t slot[EU], qi[EU];
-        uint32_t p[EU], j[EU], w[EU];
+        uint32_t p[EU], j[EU], w[EU], k[EU];
         uint32_t *wp[EU];
 #pragma unroll
         for (int u = 0; u < EU; u++) {
-            const int64_t x = base + u * 32 + lane;
+            const uint32_t x = base + u * 32 + lane;
             slot[u] = -1;
+            k[u] = 0;
             if (x < total) {
-                const int64_t it = g.begin + x / R;
+                const uint32_t io = x / R;
+                k[u] = x - io * R;
+                const int64_t it = g.begin + io;
                 slot[u] = g.item_slot[it];
                 p[u] = key_id(g.item_key[it]);
             }
         }
 #pragma unroll
         for (int u = 0; u < EU; u++) {
-            const int64_t x = base + u * 32 + lane;
-            j[u] = slot[u] >= 0 ? __ldg(a.adj + (size_t)p[u] * R + (int)(x % R)) : kSent;
+            j[u] = slot[u] >= 0 ? __ldg(a.adj + (size_t)p[u] * R + k[u]) : kSent;
             qi[u] = slot[u] >= 0 ? g.qlist[slot[u]] : 0;
-            if (COUNT && slot[u] >= 0 && x % R == 0 && a.stats) atomicAdd(&a.stats[qi[u]].visits_phase2, 1);
+            if (COUNT && slot[u] >= 0 && k[u] == 0 && a.stats) atomicAdd(&a.stats[qi[u]].visits_phase2, 1);
         }
 #pragma unroll
         for (int u = 0; u < EU; u++) {
@@ -220,7 +223,7 @@ __global__ void __launch_bounds__(256, 4) greedy_eval_kernel(GreedyArgs g) {
     using T = typename Acc<DT>::T;
     const SearchArgs &a = g.s;
     const int lane = lane_id();
-    const int lpv = a.lpv, sub = lane & (lpv - 1), grp = lane / lpv, ngrp = 32 / lpv;
+    const int lpv = a.lpv, sub = lane & (lpv - 1), grp = lane >> (__ffs(lpv) - 1), ngrp = 32 >> (__ffs(lpv) - 1);
     const int64_t nc = (int64_t)min(*(volatile unsigned long long *)g.ccount, (unsigned long long)g.ccap);
     const int64_t warp_g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;

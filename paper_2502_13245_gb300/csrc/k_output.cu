@@ -94,18 +94,13 @@ __device__ void bitonic_sort_smem(uint64_t *a, int m) {
     while (P < m) P <<= 1;
     for (int k = 2; k <= P; k <<= 1) {
         for (int j = k >> 1; j > 0; j >>= 1) {
+            const int lj = __ffs(j) - 1;  // j and k are powers of two: shifts and masks, no divisions
             for (int i = threadIdx.x; i < P / 2; i += blockDim.x) {
                 // i-th compare pair of this stage
-                int lo, hi;
-                if (j == (k >> 1)) {  // flip stage: pair (x, x ^ (k-1)) inside each k-block
-                    int blk = i / (k >> 1), off = i % (k >> 1);
-                    lo = blk * k + off;
-                    hi = blk * k + (k - 1 - off);
-                } else {
-                    int blk = i / j, off = i % j;
-                    lo = blk * 2 * j + off;
-                    hi = lo + j;
-                }
+                const int off = i & (j - 1);
+                const int lo = ((i >> lj) << (lj + 1)) + off;
+                // flip stage: pair (x, x ^ (k-1)) inside each k-block; otherwise (x, x + j)
+                const int hi = (j == (k >> 1)) ? lo - off + (k - 1 - off) : lo + j;
                 if (hi < m) {
                     uint64_t x = a[lo], y = a[hi];
                     if (y < x) { a[lo] = y; a[hi] = x; }

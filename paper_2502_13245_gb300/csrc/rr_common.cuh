@@ -151,7 +151,7 @@ __device__ __forceinline__ void eval_candidates(const SearchArgs &a, const uint4
                                                 int nc, uint64_t *ckey) {
     using T = typename Acc<DT>::T;
     const int lane = lane_id();
-    const int lpv = a.lpv, sub = lane & (lpv - 1), grp = lane / lpv, ngrp = 32 / lpv;
+    const int lpv = a.lpv, sub = lane & (lpv - 1), grp = lane >> (__ffs(lpv) - 1), ngrp = 32 >> (__ffs(lpv) - 1);
     for (int c0 = 0; c0 < nc; c0 += ngrp * UN) {
         uint4 v[UN][CPL];
 #pragma unroll
@@ -324,7 +324,7 @@ __device__ __forceinline__ void eval_candidates_lp(const SearchArgs &a, const fl
     constexpr int E = DT == DT_BF16 ? 8 : 16;
     constexpr int CH = 1;  // chunks per lane (lp_chunks <= 32)
     const int lane = lane_id();
-    const int lpv = a.lp_lpv, sub = lane & (lpv - 1), grp = lane / lpv, ngrp = 32 / lpv;
+    const int lpv = a.lp_lpv, sub = lane & (lpv - 1), grp = lane >> (__ffs(lpv) - 1), ngrp = 32 >> (__ffs(lpv) - 1);
     const bool l2 = a.metric == MET_L2;
     for (int c0 = 0; c0 < nc; c0 += ngrp * UN) {
         uint4 v[UN][CH];
@@ -394,17 +394,11 @@ __device__ __forceinline__ void warp_sort_keys(uint64_t *keys, int m) {
     while (P < m) P <<= 1;
     for (int k = 2; k <= P; k <<= 1) {
         for (int j = k >> 1; j > 0; j >>= 1) {
+            const int lj = __ffs(j) - 1;  // powers of two: shifts and masks
             for (int i = lane; i < P / 2; i += 32) {
-                int lo, hi;
-                if (j == (k >> 1)) {
-                    const int blk = i / (k >> 1), off = i % (k >> 1);
-                    lo = blk * k + off;
-                    hi = blk * k + (k - 1 - off);
-                } else {
-                    const int blk = i / j, off = i % j;
-                    lo = blk * 2 * j + off;
-                    hi = lo + j;
-                }
+                const int off = i & (j - 1);
+                const int lo = ((i >> lj) << (lj + 1)) + off;
+                const int hi = (j == (k >> 1)) ? lo - off + (k - 1 - off) : lo + j;
                 if (hi < m) {
                     const uint64_t x = keys[lo], y = keys[hi];
                     if (y < x) {
