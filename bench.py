@@ -359,7 +359,7 @@ def run_serve(args, cfg, ds, rr, gi, stream, dev):
     line = {"metric": "serving latency under open-loop Poisson load", "unit": "us", "higher_is_better": False,
             "value": rows[-1]["p99_us"] if rows else None, "n_gpus": 1, "dtype": str(ds.X.dtype), "data": "synthetic",
             "config": {"workload": "%s: n=%d d=%d, single-query requests, radii r/1.5r/2r" % (cfg.name, cfg.n, cfg.d),
-                       "variant": variant, "beam": beam, "workers": args.serve_workers,
+                       "variant": variant, "beam": beam, "workers": args.serve_workers, "layout": args.layout,
                        "max_batch": args.serve_max_batch, "batch_wait_us": args.serve_wait_us,
                        "seconds_per_rate": args.serve_secs, "batch_qps": batch_qps, "mix_cost": cost,
                        "results_in": "device memory" if args.serve_device else "host memory",
@@ -475,6 +475,9 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--fixed", default="", help="VARIANT:BEAM[:VL:ESR] -- skip the sweep and time this form")
     ap.add_argument("--no-tune", action="store_true", help="keep the library's default launch shape")
+    ap.add_argument("--relabel", default="bfs", choices=["bfs", "none"],
+                    help="renumber the points in breadth-first order from the start point before searching "
+                         "(rr_index_relabel; ids are reported in the caller's numbering either way)")
     ap.add_argument("--precision", type=int, default=0, choices=[0, 1, 2],
                     help="fp32 indexes: 0 exact, 1 BF16 traversal, 2 FP8-e4m3 traversal (exact fp32 recheck)")
     ap.add_argument("--serve", default="",
@@ -516,6 +519,16 @@ def main():
     torch.cuda.empty_cache()  # a radius picked in this process leaves torch's cache full
     metric = rr.RR_IP if cfg.metric == rrsynth.M_IP else rr.RR_L2
     gi = rr.Index.from_arrays(ds.X, ds.adj, ds.start, metric=metric, device=dev)
+    relabel_s = None
+    if args.relabel == "bfs":
+        t0 = time.time()
+        gi.relabel(rr.RR_ORDER_BFS)
+        relabel_s = time.time() - t0
+        if rank == 0:
+            log("index relabeled in breadth-first order in %.2fs" % relabel_s)
+    args.layout = ("points renumbered in breadth-first order from the start point (rr_index_relabel, %.1f s, "
+                   "outside the timed region); ids reported in the caller's numbering" % relabel_s
+                   if relabel_s is not None else "the caller's id order")
     if args.serve:
         if rank == 0:
             run_serve(args, cfg, ds, rr, gi, stream, dev)
@@ -772,6 +785,7 @@ def main():
                     args.precision],
                 "variant": variant, "beam": beam, "ap": best["ap"], "es_vl": form[1], "es_radius_over_r": form[2],
                 "launch_shape": tuned or "library default",
+                "layout": args.layout,
                 "phase_ms": {"beam": float(phase_ms[0]), "phase2": float(phase_ms[1]), "output": float(phase_ms[2]),
                              "total": float(phase_ms[3]), "phase2_steps": int(prof.phase2_steps),
                              "phase2_queries": int(prof.phase2_queries),

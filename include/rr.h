@@ -229,9 +229,41 @@ typedef struct {
     int32_t row_stride;    /* bytes per stored vector (16-byte aligned) */
     int32_t device;
     int64_t scratch_bytes; /* search scratch the index holds (device arenas + pinned staging); grow-only */
+    int32_t order;         /* 0, or the rr_order the index was relabeled in (rr_index_relabel) */
+    int32_t reserved;
 } rr_index_info;
 
 rr_status rr_index_info_get(const rr_index *index, rr_index_info *info);
+
+/* Point orders for rr_index_relabel. */
+typedef enum { RR_ORDER_BFS = 1 } rr_order;
+
+/* Relabel an index's points so that points close in the graph are close in
+ * device memory (a layout step of this library; the paper searches the graph
+ * in the id order it was built in).  Internal id i is the i-th point of the
+ * order; the vectors, the adjacency (entries renamed, slot order kept) and the
+ * start point move with it, and every id the library hands back -- search,
+ * server, no-alloc call, brute force -- is translated to the caller's id.  The
+ * greedy expansion's per-query visited bitmaps (Alg. 2) and the vector and
+ * adjacency gathers of every variant then touch fewer distinct sectors.
+ *   RR_ORDER_BFS  a queue-based breadth-first traversal from the start point
+ *                 that scans each row in slot order (padding skipped) and
+ *                 numbers a point when it is first reached; points it never
+ *                 reaches follow in ascending id order.
+ * What changes for results: a search on the relabeled index is the search on
+ * the relabeled arrays, so the beam phase's tie-breaks between equal keys
+ * (Alg. 1, by (distance, id)) use internal ids, and the results of a query
+ * come sorted by (distance, internal id) -- by distance, but equal distances
+ * in internal order.  rr_brute_force stays in (distance, id) order.
+ * Call it once, after rr_create_index / rr_load_index and before a server is
+ * created on the index; low-precision traversal copies are rebuilt on their
+ * next use.  Host memory: the adjacency (4nR bytes) and 13n bytes, freed on
+ * return; device memory: a second copy of the vectors and the adjacency while
+ * it runs, then 4n bytes for the id map.  Synchronous.  Errors: RR_EINVAL
+ * (unknown order, an index already relabeled, a worker view, an index with a
+ * live server, or an adjacency entry that is neither padding nor < n),
+ * RR_ENOMEM, RR_ECUDA. */
+rr_status rr_index_relabel(rr_index *index, int32_t order);
 
 /* Batched range search (Alg. 6 / Alg. 3 / plain beam search over a batch).
  *   queries    nq x d, the index's element type, host or device memory

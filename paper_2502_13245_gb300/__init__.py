@@ -30,6 +30,7 @@ RR_U8, RR_I8, RR_F32 = 0, 1, 2
 RR_L2, RR_IP = 0, 1
 RR_PREC_EXACT, RR_PREC_BF16, RR_PREC_FP8 = 0, 1, 2
 RR_ES_VISITED, RR_ES_TOP1, RR_ES_TOP10, RR_ES_TOP10_RATIO = 0, 1, 2, 3
+RR_ORDER_BFS = 1
 RR_FLAG_TRUNCATED, RR_FLAG_EARLY_STOPPED, RR_FLAG_PHASE2, RR_FLAG_CANCELED = 1, 2, 4, 8
 
 # every symbol include/rr.h declares (checked by the ABI test)
@@ -37,7 +38,7 @@ EXPORTS = ["rr_params_init", "rr_create_index", "rr_load_index", "rr_free_index"
            "rr_range_search", "rr_brute_force", "rr_result_free", "rr_last_error", "rr_last_profile",
            "rr_beam_search_noalloc", "rr_serve_cfg_init", "rr_serve_create", "rr_serve_submit", "rr_serve_poll",
            "rr_serve_collect", "rr_serve_cancel", "rr_serve_stats", "rr_serve_destroy", "rr_result_to_host",
-           "rr_abi_sizes", "rr_debug_set", "rr_build_graph"]
+           "rr_abi_sizes", "rr_debug_set", "rr_build_graph", "rr_index_relabel"]
 
 
 class RRError(RuntimeError):
@@ -101,7 +102,8 @@ class Result(ctypes.Structure):
 class IndexInfo(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("d", ctypes.c_int32), ("dtype", ctypes.c_int32), ("metric", ctypes.c_int32),
                 ("R", ctypes.c_int32), ("start", ctypes.c_int64), ("device_bytes", ctypes.c_int64),
-                ("row_stride", ctypes.c_int32), ("device", ctypes.c_int32), ("scratch_bytes", ctypes.c_int64)]
+                ("row_stride", ctypes.c_int32), ("device", ctypes.c_int32), ("scratch_bytes", ctypes.c_int64),
+                ("order", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class BuildInfo(ctypes.Structure):
@@ -135,6 +137,8 @@ def load_library(path: str | None = None):
     L.rr_free_index.argtypes = [P]
     L.rr_index_info_get.restype = ctypes.c_int
     L.rr_index_info_get.argtypes = [P, P]
+    L.rr_index_relabel.restype = ctypes.c_int
+    L.rr_index_relabel.argtypes = [P, I32]
     L.rr_range_search.restype = ctypes.c_int
     L.rr_range_search.argtypes = [P, P, I64, P, D, I32, P, P, I32, P]
     L.rr_brute_force.restype = ctypes.c_int
@@ -268,6 +272,10 @@ def rr_index_info_get(handle) -> IndexInfo:
     info = IndexInfo()
     _check(load_library().rr_index_info_get(handle, ctypes.byref(info)))
     return info
+
+
+def rr_index_relabel(handle, order=RR_ORDER_BFS):
+    _check(load_library().rr_index_relabel(handle, order))
 
 
 def _radii(nq, radius):
@@ -504,6 +512,12 @@ class Index:
     @classmethod
     def load(cls, path, device=0):
         return cls(rr_load_index(path, device))
+
+    def relabel(self, order=RR_ORDER_BFS):
+        """Renumber the points in breadth-first order from the start point (rr_index_relabel)."""
+        rr_index_relabel(self.h, order)
+        self.info = rr_index_info_get(self.h)
+        return self
 
     def close(self):
         if self.h:

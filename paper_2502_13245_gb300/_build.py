@@ -14,7 +14,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "librr.so")
 
 SOURCES = ["rr_runtime.cu", "rr_search.cu", "k_beam.cu", "k_greedy.cu", "k_doubling.cu", "k_output.cu", "k_brute.cu",
-           "k_noalloc.cu", "k_lowp.cu", "rr_serve.cu", "k_build.cu"]
+           "k_noalloc.cu", "k_lowp.cu", "rr_serve.cu", "k_build.cu", "k_relabel.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I" + os.path.join(ROOT, "include"), "-I" + CSRC]

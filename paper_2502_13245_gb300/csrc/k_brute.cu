@@ -54,7 +54,7 @@ __global__ void __launch_bounds__(256) brute_kernel(SearchArgs a, int32_t *count
             } else {
                 int64_t pos = offsets[qi] + atomicAdd(cursor + qi, 1);
                 if (pos >= offsets[qi + 1]) continue;  // never write past the query's segment
-                keys[pos] = make_key(dk, (uint32_t)p);
+                keys[pos] = make_key(dk, a.ext ? __ldg(a.ext + p) : (uint32_t)p);
             }
         }
     }

@@ -78,7 +78,7 @@ __global__ void init_kernel(uint32_t *rkey, uint32_t *eskey, int64_t nq, uint32_
 // N of every query (sorted keys) -> the caller's fixed-stride outputs; slots past
 // the count get id 0xFFFFFFFF and distance 0.
 __global__ void emit_kernel(const uint64_t *keys, const int32_t *count, int64_t nq, int b, int is_float,
-                            int32_t *out_counts, uint32_t *out_ids, void *out_dists) {
+                            const uint32_t *ext, int32_t *out_counts, uint32_t *out_ids, void *out_dists) {
     const int lane = threadIdx.x & 31;
     const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
     for (int64_t q = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); q < nq; q += nw) {
@@ -87,7 +87,7 @@ __global__ void emit_kernel(const uint64_t *keys, const int32_t *count, int64_t 
         for (int i = lane; i < b; i += 32) {
             const size_t o = (size_t)q * b + i;
             uint64_t k = i < c ? keys[o] : 0;
-            out_ids[o] = i < c ? key_id(k) : kSent;
+            out_ids[o] = i < c ? (ext ? __ldg(ext + key_id(k)) : key_id(k)) : kSent;
             if (is_float) reinterpret_cast<float *>(out_dists)[o] = i < c ? dval_f32(key_dk(k)) : 0.f;
             else reinterpret_cast<int32_t *>(out_dists)[o] = i < c ? dval_i32(key_dk(k)) : 0;
         }
@@ -218,7 +218,7 @@ extern "C" rr_status rr_beam_search_noalloc(rr_index *ix, const void *queries, i
     const int wpc = P.tile_hint > 0 ? std::min(8, P.tile_hint) : 4;
     if ((s = launch_beam(a, wpc, st, ix->dtype)) != RR_OK) return s;
     int eb = (int)std::min<int64_t>((nq + 7) / 8, 152 * 16);
-    emit_kernel<<<eb, 256, 0, st>>>(a.res_keys, a.res_count, nq, b, ix->dtype == RR_F32 ? 1 : 0, out_counts, out_ids,
+    emit_kernel<<<eb, 256, 0, st>>>(a.res_keys, a.res_count, nq, b, ix->dtype == RR_F32 ? 1 : 0, ix->ext, out_counts, out_ids,
                                     out_dists);
     RR_CUDA(cudaGetLastError());
     note_launch();

@@ -50,7 +50,8 @@ __device__ __forceinline__ void decode_to(const OutArgs &o, int64_t pos, uint64_
         atomicExch(o.error, 4);
         return;
     }
-    o.ids[pos] = key_id(k);
+    const uint32_t id = key_id(k);
+    o.ids[pos] = o.ext ? __ldg(o.ext + id) : id;
     uint32_t dk = key_dk(k);
     if (o.dist_is_float) reinterpret_cast<float *>(o.dists)[pos] = dval_f32(dk);
     else reinterpret_cast<int32_t *>(o.dists)[pos] = dval_i32(dk);

@@ -92,10 +92,17 @@ struct rr_index {
     // a worker view of another index: shares the vectors, adjacency and traversal copies
     // (not freed with it) and owns its own scratch, so views can search concurrently
     bool shared_data = false;
+    // relabeled index: ext[internal id] = the caller's id (n entries), the caller's start point and the
+    // order used; the parent of a worker view, and how many views of this index are alive
+    uint32_t *ext = nullptr;
+    int64_t start_ext = 0;
+    int32_t order = 0;
+    int32_t live_views = 0;
+    rr_index *parent = nullptr;
 };
 
 namespace rr {
-rr_index *index_worker_view(const rr_index *parent);
+rr_index *index_worker_view(rr_index *parent);
 }  // namespace rr
 
 namespace rr {
@@ -152,6 +159,7 @@ struct SearchArgs {
     uint64_t *vis_out;
     int32_t vis_cap;
     int32_t *vis_count;
+    const uint32_t *ext;      // exhaustive scan of a relabeled index: internal id -> caller's id
 };
 
 rr_status ensure_lowp(rr_index *ix, int prec, cudaStream_t st);
@@ -263,6 +271,7 @@ struct OutArgs {
     uint8_t *flags;
     int64_t total;            // entries in ids / dists (and in the sort keys); writes beyond are refused
     int32_t *error;           // device status word: set to 4 if a write would leave the arrays
+    const uint32_t *ext;      // relabeled index: internal id -> caller's id (nullptr: ids pass through)
 };
 // copy sorted per-query key slots (stride per query) into the CSR
 rr_status launch_copy_slots(const OutArgs &o, const uint64_t *keys, int64_t stride, const int32_t *count,

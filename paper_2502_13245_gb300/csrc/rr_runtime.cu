@@ -288,8 +288,11 @@ rr_status rr_free_index(rr_index *ix) {
         ix->lp_bf16 = ix->lp_fp8 = nullptr;
         ix->lp_fp8_info = nullptr;
         ix->lp_stats = nullptr;
+        ix->ext = nullptr;
+        if (ix->parent) ix->parent->live_views--;
     }
     if (ix->vec) cudaFree(ix->vec);
+    if (ix->ext) cudaFree(ix->ext);
     if (ix->adj) cudaFree(ix->adj);
     if (ix->arena.base) cudaFree(ix->arena.base);
     if (ix->pinned.p) cudaFreeHost(ix->pinned.p);
@@ -315,12 +318,14 @@ rr_status rr_free_index(rr_index *ix) {
 rr_status rr_index_info_get(const rr_index *ix, rr_index_info *info) {
     if (!ix || !info) { set_error("rr_index_info_get: NULL argument"); return RR_EINVAL; }
     info->n = ix->n; info->d = ix->d; info->dtype = ix->dtype; info->metric = ix->metric; info->R = ix->R;
-    info->start = ix->start; info->device_bytes = ix->device_bytes; info->row_stride = ix->row_stride;
+    info->start = ix->order ? ix->start_ext : ix->start; info->device_bytes = ix->device_bytes; info->row_stride = ix->row_stride;
     info->device = ix->device;
     info->scratch_bytes = (int64_t)ix->arena.cap + (int64_t)ix->phase2.bytes + (int64_t)ix->item_key.bytes +
                           (int64_t)ix->item_slot.bytes + (int64_t)ix->outbuf.bytes + (int64_t)ix->dbl_s[0].bytes +
                           (int64_t)ix->dbl_s[1].bytes + (int64_t)ix->dbl_tmp.bytes + (int64_t)ix->cand.bytes + (int64_t)ix->dbl_seen.bytes +
                           (int64_t)ix->pinned.cap;
+    info->order = ix->order;
+    info->reserved = 0;
     return RR_OK;
 }
 
@@ -407,7 +412,7 @@ rr_status rr_result_free(rr_result *r) {
 }  // extern "C"
 
 namespace rr {
-rr_index *index_worker_view(const rr_index *p) {
+rr_index *index_worker_view(rr_index *p) {
     rr_index *v = new (std::nothrow) rr_index();
     if (!v) return nullptr;
     v->n = p->n; v->d = p->d; v->dtype = p->dtype; v->metric = p->metric; v->R = p->R; v->start = p->start;
@@ -415,7 +420,10 @@ rr_index *index_worker_view(const rr_index *p) {
     v->lp_bf16 = p->lp_bf16; v->lp_bf16_stride = p->lp_bf16_stride;
     v->lp_fp8 = p->lp_fp8; v->lp_fp8_stride = p->lp_fp8_stride; v->lp_fp8_info = p->lp_fp8_info;
     v->lp_stats = p->lp_stats; v->max_norm = p->max_norm; v->max_abs = p->max_abs;
+    v->ext = p->ext; v->start_ext = p->start_ext; v->order = p->order;
     v->shared_data = true;
+    v->parent = p;
+    p->live_views++;
     return v;
 }
 }  // namespace rr

@@ -599,7 +599,7 @@ extern "C" rr_status rr_range_search(rr_index *ix, const void *queries, int64_t 
     void *dists = nullptr;
     const bool items = np2 > 0 && (greedy || doubling);
     if ((s = scan_and_alloc(S, &total, &ids, &dists, items ? 1 : 0)) != RR_OK) return S.fail(s);
-    OutArgs o{nq, S.offsets, ix->dtype == RR_F32 ? 1 : 0, ids, dists, S.flags, total, S.a.error};
+    OutArgs o{nq, S.offsets, ix->dtype == RR_F32 ? 1 : 0, ids, dists, S.flags, total, S.a.error, ix->ext};
     if ((s = launch_copy_slots(o, a.res_keys, a.beam, a.res_count, nullptr, (int32_t)nq, S.st)) != RR_OK) return S.fail(s);
     if (items) {
         uint64_t *tmp = (uint64_t *)ix->outbuf.p;
@@ -640,6 +640,7 @@ extern "C" rr_status rr_brute_force(rr_index *ix, const void *queries, int64_t n
     rr_status s = stage(S, queries, radii, radius, true);
     if (s != RR_OK) return S.fail(s);
     SearchArgs &a = S.a;
+    a.ext = ix->ext;  // keys carry the caller's ids, so the sort below is by (distance, id)
     int32_t *counts = a.res_count, *cursor = a.p2_list;
     if ((s = launch_brute(a, counts, nullptr, nullptr, nullptr, 0, S.st, ix->dtype)) != RR_OK) return S.fail(s);
     int64_t total = 0;
@@ -648,7 +649,7 @@ extern "C" rr_status rr_brute_force(rr_index *ix, const void *queries, int64_t n
     if ((s = scan_and_alloc(S, &total, &ids, &dists, 1)) != RR_OK) return S.fail(s);
     uint64_t *tmp = (uint64_t *)ix->outbuf.p;
     if ((s = launch_brute(a, counts, S.offsets, cursor, tmp, 1, S.st, ix->dtype)) != RR_OK) return S.fail(s);
-    OutArgs o{nq, S.offsets, ix->dtype == RR_F32 ? 1 : 0, ids, dists, S.flags, total, S.a.error};
+    OutArgs o{nq, S.offsets, ix->dtype == RR_F32 ? 1 : 0, ids, dists, S.flags, total, S.a.error, nullptr};
     // every query is a segment to sort: list = identity
     int32_t *ident = (int32_t *)ix->arena.take((size_t)std::max<int64_t>(nq, 1) * 4);
     if (!ident) { set_error("internal: arena sizing"); return S.fail(RR_EINTERNAL); }
