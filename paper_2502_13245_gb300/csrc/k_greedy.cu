@@ -40,10 +40,7 @@ __global__ void greedy_init_kernel(GreedyArgs g) {
         g.item_key[t] = k;
         g.item_slot[t] = slot;
         mark_bit(g.seen + (size_t)slot * g.seen_words, key_id(k));
-        if (i == 0) {
-            g.slot_count[slot] = b;
-            g.slot_trunc[slot] = 0;
-        }
+        if (i == 0) g.slot_trunc[slot] = 0;
     }
 }
 
@@ -90,7 +87,6 @@ __global__ void __launch_bounds__(256) greedy_level_kernel(GreedyArgs g) {
             eval_candidates<DT, CPL, UN>(a, q, cid, nc, ckey);
             __syncwarp();
             // if d(f, q) <= r: F <- F u {f}
-            int added = 0;
             for (int c0 = 0; c0 < ne; c0 += 32) {
                 int c = c0 + lane;
                 uint64_t k = c < ne ? ckey[c] : kEmpty;
@@ -110,14 +106,11 @@ __global__ void __launch_bounds__(256) greedy_level_kernel(GreedyArgs g) {
                         g.slot_trunc[slot] = 1;
                     }
                 }
-                long long room = (long long)g.cap - (long long)basepos;
-                added += room <= 0 ? 0 : (room < cnt ? (int)room : cnt);
             }
             if (COUNT) {
                 for (int o = 16; o > 0; o >>= 1) dd += __shfl_xor_sync(0xffffffffu, dd, o);
             }
             if (lane == 0) {
-                if (added) atomicAdd(g.slot_count + slot, added);
                 if (a.stats) {
                     atomicAdd(&a.stats[qi].evals, nc);
                     if (COUNT) atomicAdd(&a.stats[qi].distinct, dd);
@@ -195,22 +188,30 @@ __global__ void __launch_bounds__(256) greedy_expand_kernel(GreedyArgs g) {
                 w[u] = *wp[u];  // bits only go from 0 to 1 during the phase: a set bit read here is final
             }
         }
+        unsigned m[EU];
+        int tot = 0;
 #pragma unroll
         for (int u = 0; u < EU; u++) {
             const uint32_t bit = 1u << (j[u] & 31);
             bool fresh = false;
             if (wp[u] && !(w[u] & bit)) fresh = !(atomicOr(wp[u], bit) & bit);
-            const unsigned m = __ballot_sync(0xffffffffu, fresh);
-            if (!m) continue;
-            unsigned long long b0 = 0;
-            if (lane == 0) b0 = atomicAdd(g.ccount, (unsigned long long)__popc(m));
-            b0 = __shfl_sync(0xffffffffu, b0, 0);
-            if (fresh) {
-                const unsigned long long pos = b0 + __popc(m & lanemask_lt());
+            m[u] = __ballot_sync(0xffffffffu, fresh);
+            tot += __popc(m[u]);
+        }
+        if (!tot) continue;
+        // one reservation for the warp's first-seen neighbours of all EU rounds
+        unsigned long long b0 = 0;
+        if (lane == 0) b0 = atomicAdd(g.ccount, (unsigned long long)tot);
+        b0 = __shfl_sync(0xffffffffu, b0, 0);
+#pragma unroll
+        for (int u = 0; u < EU; u++) {
+            if ((m[u] >> lane) & 1u) {
+                const unsigned long long pos = b0 + __popc(m[u] & lanemask_lt());
                 if (pos < (unsigned long long)g.ccap)
                     reinterpret_cast<uint4 *>(g.cand)[pos] = make_uint4(j[u], (uint32_t)slot[u], (uint32_t)qi[u], 0u);
                 else atomicExch(a.error, 7);  // the host sizes the list for the chunk: cannot happen
             }
+            b0 += __popc(m[u]);
         }
     }
 }
@@ -244,6 +245,9 @@ __global__ void __launch_bounds__(256, 4) greedy_eval_kernel(GreedyArgs g) {
             q[u] = ch ? ldg16(a.queries + (size_t)qi[u] * a.row_stride + (size_t)sub * 16) : make_uint4(0, 0, 0, 0);
             v[u] = ch ? ldg16(a.vec + (size_t)id[u] * a.row_stride + (size_t)sub * 16) : make_uint4(0, 0, 0, 0);
         }
+        uint32_t dk[UN];
+        unsigned m[UN];
+        int tot = 0;
 #pragma unroll
         for (int u = 0; u < UN; u++) {
             T sum = 0;
@@ -251,29 +255,35 @@ __global__ void __launch_bounds__(256, 4) greedy_eval_kernel(GreedyArgs g) {
             else Acc<DT>::ip(sum, q[u], v[u]);
             sum = group_sum(sum, lpv);
             const int64_t c = c0 + grp + (int64_t)ngrp * u;
-            const uint32_t dk = finish_dk(sum, a.metric);
+            dk[u] = finish_dk(sum, a.metric);
             const bool lead = sub == 0 && c < nc;
-            const bool in = lead && dk <= a.rkey[qi[u]];
+            const bool in = lead && dk[u] <= a.rkey[qi[u]];
             if (COUNT && lead && a.stats) {
                 atomicAdd(&a.stats[qi[u]].evals, 1);
                 if (mark_bit(a.count_bits + (size_t)qi[u] * a.words_per_q, id[u]))
                     atomicAdd(&a.stats[qi[u]].distinct, 1);
             }
-            const unsigned m = __ballot_sync(0xffffffffu, in);
-            if (!m) continue;
-            unsigned long long b0 = 0;
-            if (lane == 0) b0 = atomicAdd(g.tail, (unsigned long long)__popc(m));
-            b0 = __shfl_sync(0xffffffffu, b0, 0);
-            if (in) {
-                const unsigned long long pos = b0 + __popc(m & lanemask_lt());
+            m[u] = __ballot_sync(0xffffffffu, in);
+            tot += __popc(m[u]);
+        }
+        if (!tot) continue;
+        // one reservation for the warp's in-range points of all UN rounds; per-query counts are taken
+        // from the item list after the last level (count_items_kernel)
+        unsigned long long b0 = 0;
+        if (lane == 0) b0 = atomicAdd(g.tail, (unsigned long long)tot);
+        b0 = __shfl_sync(0xffffffffu, b0, 0);
+#pragma unroll
+        for (int u = 0; u < UN; u++) {
+            if ((m[u] >> lane) & 1u) {
+                const unsigned long long pos = b0 + __popc(m[u] & lanemask_lt());
                 if (pos < (unsigned long long)g.cap) {
-                    g.item_key[pos] = make_key(dk, id[u]);
+                    g.item_key[pos] = make_key(dk[u], id[u]);
                     g.item_slot[pos] = slot[u];
-                    atomicAdd(g.slot_count + slot[u], 1);
                 } else {
                     g.slot_trunc[slot[u]] = 1;
                 }
             }
+            b0 += __popc(m[u]);
         }
     }
 }
@@ -293,6 +303,27 @@ rr_status two_pass_t(const GreedyArgs &g, cudaStream_t st) {
     RR_CUDA(cudaGetLastError());
     note_launch(2);
     return RR_OK;
+}
+
+// slot_count[s] += the items of slot s among items [0, n).  Items are appended in runs of one slot (a
+// warp's reservation holds consecutive pairs of one item, mostly), so each warp adds one count per run it
+// sees rather than one per item.
+__global__ void count_items_kernel(const int32_t *item_slot, int64_t n, int32_t *slot_count) {
+    const int lane = lane_id();
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) & ~(int64_t)31; base < n; base += stride) {
+        const int64_t t = base + lane;
+        const int32_t s = t < n ? item_slot[t] : -1;
+        const int32_t prev = __shfl_up_sync(0xffffffffu, s, 1);
+        const bool head = t < n && (lane == 0 || prev != s);
+        const unsigned hm = __ballot_sync(0xffffffffu, head);
+        if (head) {
+            // the run ends at the next head of this warp, or after the warp's last item
+            const unsigned later = hm & ~((2u << lane) - 1u);
+            const int stop = later ? __ffs(later) - 1 : (n - base < 32 ? (int)(n - base) : 32);
+            atomicAdd(slot_count + s, stop - lane);
+        }
+    }
 }
 
 __global__ void set_counts_kernel(int32_t *res_count, uint8_t *flags, const int32_t *qlist, const int32_t *slot_count,
@@ -343,6 +374,15 @@ rr_status launch_greedy_level(const GreedyArgs &g, cudaStream_t st, int dtype_co
     }
     set_error("greedy phase: unsupported element type %d", dtype_code);
     return RR_EINVAL;
+}
+
+rr_status launch_count_items(const int32_t *item_slot, int64_t n, int32_t *slot_count, cudaStream_t st) {
+    if (n <= 0) return RR_OK;
+    const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 16));
+    count_items_kernel<<<(unsigned)blocks, 256, 0, st>>>(item_slot, n, slot_count);
+    RR_CUDA(cudaGetLastError());
+    note_launch();
+    return RR_OK;
 }
 
 rr_status launch_set_counts(int32_t *res_count, uint8_t *flags, const int32_t *qlist, const int32_t *slot_count,

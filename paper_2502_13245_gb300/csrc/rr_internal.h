@@ -286,6 +286,8 @@ rr_status launch_sort_segments(const OutArgs &o, uint64_t *tmp_keys, const int32
 // Brute force (Def. 2.1): count pass and fill pass over all (query, point) pairs.
 rr_status launch_brute(const SearchArgs &a, int32_t *counts, const int64_t *offsets, int32_t *cursor,
                        uint64_t *keys, int fill, cudaStream_t s, int dtype_code);
+// after the greedy levels: slot_count[s] += the items of slot s among items [0, n)
+rr_status launch_count_items(const int32_t *item_slot, int64_t n, int32_t *slot_count, cudaStream_t s);
 // after phase 2: res_count[qlist[s]] = slot_count[s]; truncated slots flag their query
 rr_status launch_set_counts(int32_t *res_count, uint8_t *flags, const int32_t *qlist, const int32_t *slot_count,
                             const int32_t *slot_trunc, int32_t n, cudaStream_t s);

@@ -338,6 +338,8 @@ rr_status run_greedy(Search &S, int32_t np2, GreedyOut &go) {
         }
     }
     go.nitems = end;
+    RR_CUDA(cudaMemsetAsync(g.slot_count, 0, (size_t)np2 * 4, S.st));
+    if ((s = launch_count_items(g.item_slot, end, g.slot_count, S.st)) != RR_OK) return s;
     return launch_set_counts(S.a.res_count, S.flags, a.p2_list, g.slot_count, g.slot_trunc, np2, S.st);
 }
 
