@@ -216,12 +216,126 @@ __global__ void __launch_bounds__(256) greedy_expand_kernel(GreedyArgs g) {
     }
 }
 
-// Evaluate pass: each lane group of lpv lanes takes UN candidates at a time (their query and point
-// vectors gathered before any is reduced); in-range ones are appended to the item list.
+// Expand pass for R a multiple of 32 (RR = R / 32 row words per lane): a warp takes IW consecutive items
+// per iteration and lane l the row entries l + 32 t of each, so no pair index is divided by R.  The
+// items of the warp's next iteration are loaded before this iteration's seen words are read, so the
+// item -> row -> seen-word chain of one iteration overlaps the item loads of the next.
+template <bool COUNT, int RR>
+__global__ void __launch_bounds__(256, 4) greedy_expand_rows_kernel(GreedyArgs g) {
+    constexpr int IW = RR <= 2 ? 4 : 2;  // items per warp iteration: 4 to 8 row entries per lane
+    constexpr int NP = IW * RR;          // pairs per lane and iteration
+    const SearchArgs &a = g.s;
+    const int lane = lane_id();
+    const int R = 32 * RR;
+    const int64_t nitems = g.end - g.begin;
+    const int64_t warp_g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t step = (((int64_t)gridDim.x * blockDim.x) >> 5) * IW;
+    int32_t slot[IW];
+    uint32_t p[IW];
+#pragma unroll
+    for (int i = 0; i < IW; i++) {
+        const int64_t it = warp_g * IW + i;
+        slot[i] = it < nitems ? g.item_slot[g.begin + it] : -1;
+        p[i] = it < nitems ? key_id(g.item_key[g.begin + it]) : 0u;
+    }
+    for (int64_t i0 = warp_g * IW; i0 < nitems; i0 += step) {
+        uint32_t j[NP];
+        int32_t qi[IW];
+#pragma unroll
+        for (int i = 0; i < IW; i++) {
+            qi[i] = slot[i] >= 0 ? g.qlist[slot[i]] : 0;
+#pragma unroll
+            for (int t = 0; t < RR; t++)
+                j[i * RR + t] = slot[i] >= 0 ? __ldg(a.adj + (size_t)p[i] * R + 32 * t + lane) : kSent;
+            if (COUNT && slot[i] >= 0 && lane == 0 && a.stats) atomicAdd(&a.stats[qi[i]].visits_phase2, 1);
+        }
+        // the next iteration's items
+        int32_t nslot[IW];
+        uint32_t np[IW];
+#pragma unroll
+        for (int i = 0; i < IW; i++) {
+            const int64_t it = i0 + step + i;
+            nslot[i] = it < nitems ? g.item_slot[g.begin + it] : -1;
+            np[i] = it < nitems ? key_id(g.item_key[g.begin + it]) : 0u;
+        }
+        uint32_t w[NP];
+        uint32_t *wp[NP];
+#pragma unroll
+        for (int e = 0; e < NP; e++) {
+            const int i = e / RR;  // compile-time
+            wp[e] = nullptr;
+            w[e] = 0xFFFFFFFFu;
+            if (j[e] < (uint32_t)a.n) {
+                wp[e] = g.seen + (size_t)slot[i] * g.seen_words + (j[e] >> 5);
+                w[e] = *wp[e];  // bits only go from 0 to 1 during the phase: a set bit read here is final
+            }
+        }
+        unsigned m[NP];
+        int tot = 0;
+#pragma unroll
+        for (int e = 0; e < NP; e++) {
+            const uint32_t bit = 1u << (j[e] & 31);
+            bool fresh = false;
+            if (wp[e] && !(w[e] & bit)) fresh = !(atomicOr(wp[e], bit) & bit);
+            m[e] = __ballot_sync(0xffffffffu, fresh);
+            tot += __popc(m[e]);
+        }
+        if (tot) {
+            unsigned long long b0 = 0;
+            if (lane == 0) b0 = atomicAdd(g.ccount, (unsigned long long)tot);
+            b0 = __shfl_sync(0xffffffffu, b0, 0);
+#pragma unroll
+            for (int e = 0; e < NP; e++) {
+                const int i = e / RR;
+                if ((m[e] >> lane) & 1u) {
+                    const unsigned long long pos = b0 + __popc(m[e] & lanemask_lt());
+                    if (pos < (unsigned long long)g.ccap)
+                        reinterpret_cast<uint4 *>(g.cand)[pos] =
+                            make_uint4(j[e], (uint32_t)slot[i], (uint32_t)qi[i], 0u);
+                    else atomicExch(a.error, 7);  // the host sizes the list for the chunk: cannot happen
+                }
+                b0 += __popc(m[e]);
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < IW; i++) {
+            slot[i] = nslot[i];
+            p[i] = np[i];
+        }
+    }
+}
+
+template <bool COUNT>
+void launch_expand(const GreedyArgs &g, int64_t pairs, cudaStream_t st) {
+    const int R = g.s.R;
+    if (R % 32 == 0 && R <= 128) {
+        // a grid of resident CTAs that loops, so the next-iteration loads have an iteration to hide behind
+        const int64_t per_warp = R <= 64 ? 4 : 2;
+        const int64_t items = g.end - g.begin;
+        const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((items + 8 * per_warp - 1) / (8 * per_warp),
+                                                                      152 * 4));
+        switch (R / 32) {
+            case 1: greedy_expand_rows_kernel<COUNT, 1><<<(unsigned)blocks, 256, 0, st>>>(g); return;
+            case 2: greedy_expand_rows_kernel<COUNT, 2><<<(unsigned)blocks, 256, 0, st>>>(g); return;
+            case 3: greedy_expand_rows_kernel<COUNT, 3><<<(unsigned)blocks, 256, 0, st>>>(g); return;
+            default: greedy_expand_rows_kernel<COUNT, 4><<<(unsigned)blocks, 256, 0, st>>>(g); return;
+        }
+    }
+    int64_t blocks = (pairs + 1023) / 1024;  // 4 pairs per thread and iteration
+    blocks = std::max<int64_t>(1, std::min<int64_t>(blocks, 152 * 16));
+    greedy_expand_kernel<COUNT><<<(unsigned)blocks, 256, 0, st>>>(g);
+}
+
+// Evaluate pass: each lane group of lpv lanes takes UN candidates at a time (their vectors gathered
+// before any is reduced); in-range ones are appended to the item list.  8-bit sums are exact integers,
+// so the UN partial sums of a group are combined by a reduce-scatter (each exchange with the partner
+// lane halves the values a lane holds) and each writer lane ends with whole candidates, decided and
+// appended by one ballot and one list reservation per warp iteration.
 template <int DT, bool COUNT>
-__global__ void __launch_bounds__(256, 4) greedy_eval_kernel(GreedyArgs g) {
-    constexpr int UN = 4;
+__global__ void __launch_bounds__(256, 3) greedy_eval_kernel(GreedyArgs g) {
+    constexpr int UN = 8;
     using T = typename Acc<DT>::T;
+    static_assert(std::is_integral<T>::value, "the two-pass levels run on 8-bit indexes");
     const SearchArgs &a = g.s;
     const int lane = lane_id();
     const int lpv = a.lpv, sub = lane & (lpv - 1), grp = lane >> (__ffs(lpv) - 1), ngrp = 32 >> (__ffs(lpv) - 1);
@@ -229,61 +343,98 @@ __global__ void __launch_bounds__(256, 4) greedy_eval_kernel(GreedyArgs g) {
     const int64_t warp_g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int64_t per = (int64_t)ngrp * UN;
+    const uint4 *cand = reinterpret_cast<const uint4 *>(g.cand);
+    // the lane's chunk of the query of its last candidate: consecutive candidates mostly share a query
+    // (the expand pass writes an item's first-seen neighbours together), so it is reloaded on change only
+    int32_t qcur = -1;
+    uint4 qv = make_uint4(0, 0, 0, 0);
+    const int cnt = lpv >= UN ? 1 : UN / lpv;  // candidates a writer lane ends with
+    const bool writer = lpv <= UN || (sub & (lpv / UN - 1)) == 0;
     for (int64_t c0 = warp_g * per; c0 < nc; c0 += nwarps * per) {
-        uint4 q[UN], v[UN];
-        int32_t slot[UN], qi[UN];
-        uint32_t id[UN];
+        uint4 v[UN];
+        int32_t qi[UN];
 #pragma unroll
         for (int u = 0; u < UN; u++) {
             const int64_t c = c0 + grp + (int64_t)ngrp * u;
             const bool ok = c < nc;
-            const uint4 e = ok ? reinterpret_cast<const uint4 *>(g.cand)[c] : make_uint4(0u, 0u, 0u, 0u);
-            id[u] = e.x;
-            slot[u] = (int32_t)e.y;
-            qi[u] = (int32_t)e.z;
-            const bool ch = ok && sub < a.row_chunks;
-            q[u] = ch ? ldg16(a.queries + (size_t)qi[u] * a.row_stride + (size_t)sub * 16) : make_uint4(0, 0, 0, 0);
-            v[u] = ch ? ldg16(a.vec + (size_t)id[u] * a.row_stride + (size_t)sub * 16) : make_uint4(0, 0, 0, 0);
+            const uint4 e = ok ? cand[c] : make_uint4(0u, 0u, 0u, 0u);
+            qi[u] = ok ? (int32_t)e.z : -1;
+            v[u] = ok && sub < a.row_chunks ? ldg16(a.vec + (size_t)e.x * a.row_stride + (size_t)sub * 16)
+                                            : make_uint4(0, 0, 0, 0);
         }
-        uint32_t dk[UN];
-        unsigned m[UN];
-        int tot = 0;
+        T s[UN];
 #pragma unroll
         for (int u = 0; u < UN; u++) {
-            T sum = 0;
-            if (a.metric == MET_L2) Acc<DT>::l2(sum, q[u], v[u]);
-            else Acc<DT>::ip(sum, q[u], v[u]);
-            sum = group_sum(sum, lpv);
-            const int64_t c = c0 + grp + (int64_t)ngrp * u;
-            dk[u] = finish_dk(sum, a.metric);
-            const bool lead = sub == 0 && c < nc;
-            const bool in = lead && dk[u] <= a.rkey[qi[u]];
-            if (COUNT && lead && a.stats) {
-                atomicAdd(&a.stats[qi[u]].evals, 1);
-                if (mark_bit(a.count_bits + (size_t)qi[u] * a.words_per_q, id[u]))
-                    atomicAdd(&a.stats[qi[u]].distinct, 1);
+            if (qi[u] >= 0 && qi[u] != qcur) {
+                qcur = qi[u];
+                qv = sub < a.row_chunks ? ldg16(a.queries + (size_t)qcur * a.row_stride + (size_t)sub * 16)
+                                        : make_uint4(0, 0, 0, 0);
             }
-            m[u] = __ballot_sync(0xffffffffu, in);
-            tot += __popc(m[u]);
+            s[u] = 0;
+            if (a.metric == MET_L2) Acc<DT>::l2(s[u], qv, v[u]);
+            else Acc<DT>::ip(s[u], qv, v[u]);
+        }
+        int base = 0, mk = lpv >> 1;
+#pragma unroll
+        for (int hh = UN >> 1; hh >= 1; hh >>= 1) {
+            if (mk >= 1) {  // warp-uniform
+                const bool up = (sub & mk) != 0;
+#pragma unroll
+                for (int i = 0; i < hh; i++) {
+                    const T send = up ? s[i] : s[i + hh];
+                    const T keep = up ? s[i + hh] : s[i];
+                    s[i] = keep + __shfl_xor_sync(0xffffffffu, send, mk);
+                }
+                if (up) base += hh;
+                mk >>= 1;
+            }
+        }
+        for (; mk >= 1; mk >>= 1) s[0] += __shfl_xor_sync(0xffffffffu, s[0], mk);  // lpv > UN
+        // lane holds the totals of candidates u = base .. base + cnt - 1 of its group
+        uint32_t dk[UN / 2 > 0 ? UN / 2 : 1], id[UN / 2 > 0 ? UN / 2 : 1];
+        int32_t slot[UN / 2 > 0 ? UN / 2 : 1];
+        unsigned m[UN / 2 > 0 ? UN / 2 : 1];
+        int tot = 0;
+#pragma unroll
+        for (int i = 0; i < UN / 2; i++) {
+            m[i] = 0;
+            if (i >= cnt) break;  // warp-uniform
+            const int64_t c = c0 + grp + (int64_t)ngrp * (base + i);
+            const bool lead = writer && c < nc;
+            bool in = false;
+            if (lead) {
+                const uint4 e = cand[c];  // the candidate this lane now holds (an L1 hit: read above)
+                id[i] = e.x;
+                slot[i] = (int32_t)e.y;
+                dk[i] = finish_dk(s[i], a.metric);
+                in = dk[i] <= a.rkey[e.z];
+                if (COUNT && a.stats) {
+                    atomicAdd(&a.stats[e.z].evals, 1);
+                    if (mark_bit(a.count_bits + (size_t)e.z * a.words_per_q, e.x)) atomicAdd(&a.stats[e.z].distinct, 1);
+                }
+            }
+            m[i] = __ballot_sync(0xffffffffu, in);
+            tot += __popc(m[i]);
         }
         if (!tot) continue;
-        // one reservation for the warp's in-range points of all UN rounds; per-query counts are taken
-        // from the item list after the last level (count_items_kernel)
+        // one reservation for the warp's in-range points; per-query counts are taken from the item list
+        // after the last level (count_items_kernel)
         unsigned long long b0 = 0;
         if (lane == 0) b0 = atomicAdd(g.tail, (unsigned long long)tot);
         b0 = __shfl_sync(0xffffffffu, b0, 0);
 #pragma unroll
-        for (int u = 0; u < UN; u++) {
-            if ((m[u] >> lane) & 1u) {
-                const unsigned long long pos = b0 + __popc(m[u] & lanemask_lt());
+        for (int i = 0; i < UN / 2; i++) {
+            if (i >= cnt) break;
+            if ((m[i] >> lane) & 1u) {
+                const unsigned long long pos = b0 + __popc(m[i] & lanemask_lt());
                 if (pos < (unsigned long long)g.cap) {
-                    g.item_key[pos] = make_key(dk[u], id[u]);
-                    g.item_slot[pos] = slot[u];
+                    g.item_key[pos] = make_key(dk[i], id[i]);
+                    g.item_slot[pos] = slot[i];
                 } else {
-                    g.slot_trunc[slot[u]] = 1;
+                    g.slot_trunc[slot[i]] = 1;
                 }
             }
-            b0 += __popc(m[u]);
+            b0 += __popc(m[i]);
         }
     }
 }
@@ -291,10 +442,8 @@ __global__ void __launch_bounds__(256, 4) greedy_eval_kernel(GreedyArgs g) {
 template <int DT>
 rr_status two_pass_t(const GreedyArgs &g, cudaStream_t st) {
     const int64_t pairs = (g.end - g.begin) * (int64_t)g.s.R;
-    int64_t blocks = (pairs + 1023) / 1024;  // 4 pairs per thread and iteration
-    blocks = std::max<int64_t>(1, std::min<int64_t>(blocks, 152 * 16));
-    if (g.s.count_bits) greedy_expand_kernel<true><<<(unsigned)blocks, 256, 0, st>>>(g);
-    else greedy_expand_kernel<false><<<(unsigned)blocks, 256, 0, st>>>(g);
+    if (g.s.count_bits) launch_expand<true>(g, pairs, st);
+    else launch_expand<false>(g, pairs, st);
     RR_CUDA(cudaGetLastError());
     // the candidate count is read on the device; the grid covers a full level's worth of candidates
     int64_t eblocks = std::max<int64_t>(1, std::min<int64_t>((pairs + 255) / 256, 152 * 16));

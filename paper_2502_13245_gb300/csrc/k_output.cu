@@ -74,12 +74,32 @@ __global__ void copy_slots_kernel(OutArgs o, const uint64_t *keys, int64_t strid
     }
 }
 
+// Items to the CSR segments of their queries (unsorted within a segment).  Items come in runs of one
+// slot, so the first lane of each run in a warp reserves the run's positions with one atomic.
 __global__ void scatter_items_kernel(OutArgs o, const uint64_t *item_key, const int32_t *item_slot, int64_t nitems,
                                      const int32_t *qlist, int32_t *cursor, uint64_t *tmp) {
-    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nitems; t += (int64_t)gridDim.x * blockDim.x) {
-        int32_t s = item_slot[t];
-        int64_t q = qlist[s];
-        int64_t pos = o.offsets[q] + atomicAdd(cursor + s, 1);
+    const int lane = lane_id();
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) & ~(int64_t)31; base < nitems; base += stride) {
+        const int64_t t = base + lane;
+        const bool ok = t < nitems;
+        const int32_t s = ok ? item_slot[t] : -1;
+        const int32_t prev = __shfl_up_sync(0xffffffffu, s, 1);
+        const bool head = ok && (lane == 0 || prev != s);
+        const unsigned hm = __ballot_sync(0xffffffffu, head);
+        int32_t r0 = 0;
+        if (head) {
+            const unsigned later = hm & ~((2u << lane) - 1u);
+            const int stop = later ? __ffs(later) - 1 : (nitems - base < 32 ? (int)(nitems - base) : 32);
+            r0 = atomicAdd(cursor + s, stop - lane);
+        }
+        // the head of this lane's run: the last head at or before the lane (lane 0 is one when ok)
+        const unsigned upto = hm & ((2u << lane) - 1u);
+        const int h = upto ? 31 - __clz(upto) : 0;
+        r0 = __shfl_sync(0xffffffffu, r0, h);
+        if (!ok) continue;
+        const int64_t q = qlist[s];
+        const int64_t pos = o.offsets[q] + r0 + (lane - h);
         if (pos < 0 || pos >= o.offsets[q + 1]) {
             atomicExch(o.error, 4);
             continue;
@@ -172,7 +192,8 @@ rr_status launch_sort_segments(const OutArgs &o, uint64_t *tmp, const int32_t *q
                                cudaStream_t st) {
     if (nlist <= 0) return RR_OK;
     // keys: the largest shared-memory block a CTA may take (227 KB), so segments of up to 29,056 results
-    // are sorted on chip; longer ones in place in global memory
+    // are sorted on chip; longer ones in place in global memory.  (Size classes in three launches with
+    // smaller blocks for short segments measured slower: each launch has its own tail.)
     int dev = 0, optin = 0;
     RR_CUDA(cudaGetDevice(&dev));
     RR_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
