@@ -390,24 +390,20 @@ __global__ void __launch_bounds__(256, 3) greedy_eval_kernel(GreedyArgs g) {
             }
         }
         for (; mk >= 1; mk >>= 1) s[0] += __shfl_xor_sync(0xffffffffu, s[0], mk);  // lpv > UN
-        // lane holds the totals of candidates u = base .. base + cnt - 1 of its group
-        uint32_t dk[UN / 2 > 0 ? UN / 2 : 1], id[UN / 2 > 0 ? UN / 2 : 1];
-        int32_t slot[UN / 2 > 0 ? UN / 2 : 1];
-        unsigned m[UN / 2 > 0 ? UN / 2 : 1];
+        // lane holds the totals of candidates u = base .. base + cnt - 1 of its group (cnt = UN / lpv when
+        // a row has fewer than UN chunks, up to UN for one-chunk rows); the candidate entries are read
+        // again where needed (L1 hits) rather than kept in registers
+        unsigned m[UN];
         int tot = 0;
 #pragma unroll
-        for (int i = 0; i < UN / 2; i++) {
+        for (int i = 0; i < UN; i++) {
             m[i] = 0;
             if (i >= cnt) break;  // warp-uniform
             const int64_t c = c0 + grp + (int64_t)ngrp * (base + i);
-            const bool lead = writer && c < nc;
             bool in = false;
-            if (lead) {
-                const uint4 e = cand[c];  // the candidate this lane now holds (an L1 hit: read above)
-                id[i] = e.x;
-                slot[i] = (int32_t)e.y;
-                dk[i] = finish_dk(s[i], a.metric);
-                in = dk[i] <= a.rkey[e.z];
+            if (writer && c < nc) {
+                const uint4 e = cand[c];
+                in = finish_dk(s[i], a.metric) <= a.rkey[e.z];
                 if (COUNT && a.stats) {
                     atomicAdd(&a.stats[e.z].evals, 1);
                     if (mark_bit(a.count_bits + (size_t)e.z * a.words_per_q, e.x)) atomicAdd(&a.stats[e.z].distinct, 1);
@@ -423,15 +419,16 @@ __global__ void __launch_bounds__(256, 3) greedy_eval_kernel(GreedyArgs g) {
         if (lane == 0) b0 = atomicAdd(g.tail, (unsigned long long)tot);
         b0 = __shfl_sync(0xffffffffu, b0, 0);
 #pragma unroll
-        for (int i = 0; i < UN / 2; i++) {
+        for (int i = 0; i < UN; i++) {
             if (i >= cnt) break;
             if ((m[i] >> lane) & 1u) {
+                const uint4 e = cand[c0 + grp + (int64_t)ngrp * (base + i)];
                 const unsigned long long pos = b0 + __popc(m[i] & lanemask_lt());
                 if (pos < (unsigned long long)g.cap) {
-                    g.item_key[pos] = make_key(dk[i], id[i]);
-                    g.item_slot[pos] = slot[i];
+                    g.item_key[pos] = make_key(finish_dk(s[i], a.metric), e.x);
+                    g.item_slot[pos] = (int32_t)e.y;
                 } else {
-                    g.slot_trunc[slot[i]] = 1;
+                    g.slot_trunc[e.y] = 1;
                 }
             }
             b0 += __popc(m[i]);

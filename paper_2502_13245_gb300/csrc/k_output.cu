@@ -109,12 +109,64 @@ __global__ void scatter_items_kernel(OutArgs o, const uint64_t *item_key, const 
 }
 
 // Bitonic sort with "flip" first stages, so every compare puts the smaller key
-// at the lower index and a virtual +inf padding past m never moves.
+// at the lower index and a virtual +inf padding past m never moves.  The
+// stages whose pairs lie inside one 64-key region (every stage of the levels
+// k <= 64, and the j <= 32 stages of every later level) run in registers: a
+// warp holds a region as keys r + lane and r + 32 + lane and exchanges them by
+// shuffles, so only the j >= 64 stages go through memory with a block barrier.
+
+// one stage on a warp's 64-key region (x = key lane, y = key 32 + lane)
+__device__ __forceinline__ void region_stage(uint64_t &x, uint64_t &y, int lane, int k, int j) {
+    const bool flip = j == (k >> 1);
+    if (j == 32) {
+        if (flip) {  // k = 64: key lane pairs with key 63 - lane, the y of lane 31 - lane
+            const uint64_t oy = __shfl_xor_sync(0xffffffffu, y, 31);
+            const uint64_t ox = __shfl_xor_sync(0xffffffffu, x, 31);
+            x = oy < x ? oy : x;
+            y = ox > y ? ox : y;
+        } else {
+            const uint64_t lo = x < y ? x : y, hi = x < y ? y : x;
+            x = lo;
+            y = hi;
+        }
+    } else {
+        const int partner = flip ? k - 1 : j;  // pair (t, t ^ (k-1)) or (t, t + j), both within 32 keys
+        const uint64_t ox = __shfl_xor_sync(0xffffffffu, x, partner);
+        const uint64_t oy = __shfl_xor_sync(0xffffffffu, y, partner);
+        const bool upper = (lane & j) != 0;  // the higher index of the pair keeps the larger key
+        x = upper ? (ox > x ? ox : x) : (ox < x ? ox : x);
+        y = upper ? (oy > y ? oy : y) : (oy < y ? oy : y);
+    }
+}
+
+// stages (k, j) for j from j_hi down to 1 on every 64-key region (keys past m read as +inf, not stored)
+__device__ __forceinline__ void region_pass(uint64_t *a, int m, int P, int k, int j_hi, bool levels_upto_64) {
+    const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int r = threadIdx.x >> 5; r < (P >> 6); r += nw) {
+        const int i0 = (r << 6) + lane, i1 = i0 + 32;
+        uint64_t x = i0 < m ? a[i0] : ~0ull, y = i1 < m ? a[i1] : ~0ull;
+        if (levels_upto_64) {
+#pragma unroll
+            for (int kk = 2; kk <= 64; kk <<= 1)
+#pragma unroll
+                for (int j = kk >> 1; j > 0; j >>= 1) region_stage(x, y, lane, kk, j);
+        } else {
+#pragma unroll
+            for (int j = 32; j > 0; j >>= 1)
+                if (j <= j_hi) region_stage(x, y, lane, k, j);
+        }
+        if (i0 < m) a[i0] = x;
+        if (i1 < m) a[i1] = y;
+    }
+}
+
 __device__ void bitonic_sort_smem(uint64_t *a, int m) {
-    int P = 1;
+    int P = 64;
     while (P < m) P <<= 1;
-    for (int k = 2; k <= P; k <<= 1) {
-        for (int j = k >> 1; j > 0; j >>= 1) {
+    region_pass(a, m, P, 64, 32, true);
+    __syncthreads();
+    for (int k = 128; k <= P; k <<= 1) {
+        for (int j = k >> 1; j >= 64; j >>= 1) {
             const int lj = __ffs(j) - 1;  // j and k are powers of two: shifts and masks, no divisions
             for (int i = threadIdx.x; i < P / 2; i += blockDim.x) {
                 // i-th compare pair of this stage
@@ -129,6 +181,8 @@ __device__ void bitonic_sort_smem(uint64_t *a, int m) {
             }
             __syncthreads();
         }
+        region_pass(a, m, P, k, 32, false);
+        __syncthreads();
     }
 }
 
