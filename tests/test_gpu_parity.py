@@ -342,3 +342,26 @@ def test_c0_warm_doubling_bit_exact(rr, c0, c0_index, c0_oracle, variant, beam):
     lit = c0_index.range_search(c0.Q, c0.radius, variant.replace("_warm", ""), beam=beam, b_max=4096,
                                 collect_stats=1)
     assert res.stats["visits_beam"].sum() <= lit.stats["visits_beam"].sum()
+
+
+@pytest.mark.parametrize("d", [16, 32, 48, 64, 200, 512])
+def test_greedy_levels_at_every_row_width(rr, d):
+    """The greedy levels split a vector over 1 to 32 lanes (16 bytes each, rounded up to a power of two)
+    and a writer lane ends with 8 / lanes candidates: every split is compared with the oracle bit for bit
+    (graph degree 32 takes the row-major expand pass, 24 the per-pair one)."""
+    rng = np.random.default_rng(d)
+    n = 1500
+    C = rng.integers(0, 256, size=(6, d))
+    X = np.clip(C[rng.integers(0, 6, n)] + rng.integers(-12, 13, size=(n, d)), 0, 255).astype(np.uint8)
+    Q = np.clip(C[rng.integers(0, 6, 40)] + rng.integers(-12, 13, size=(40, d)), 0, 255).astype(np.uint8)
+    d2 = ((X[None].astype(np.int64) - Q[:, None].astype(np.int64)) ** 2).sum(-1)
+    r = float(np.percentile(d2, 8))
+    for R in (32, 24):
+        adj, start = rrsynth.build_graph(X, R, 32, 1.2, seed=d)
+        gi, oi = _tiny_index(rr, X, adj, start)
+        for v in ("greedy", "greedy_es"):
+            o_ids, o_d, _ = oracle.range_search(oi, Q, r, v, beam=8)
+            res = gi.range_search(Q, r, v, beam=8)
+            assert sum(len(x) for x in o_ids) > 40 * 8  # phase 2 runs
+            assert_same(res, o_ids, o_d, len(Q))
+        gi.close()
