@@ -26,8 +26,10 @@ namespace rr {
 
 namespace {
 
+// per warp (R here counts the candidates of one iteration), rounded to 16 bytes so that every warp's
+// 8-byte arrays stay aligned for any degree
 __host__ __device__ inline size_t warp_smem_bytes(int bmax, int R, int hlg) {
-    return (size_t)bmax * 8 + (size_t)2 * R * 8 + (size_t)3 * R * 4 + ((size_t)4 << hlg);
+    return ((size_t)bmax * 8 + (size_t)2 * R * 8 + (size_t)3 * R * 4 + ((size_t)4 << hlg) + 15) & ~(size_t)15;
 }
 
 // number of a[t] with (a[t] | 1) < k1

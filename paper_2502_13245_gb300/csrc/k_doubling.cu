@@ -69,7 +69,10 @@ struct RSmem {
     uint32_t *cid;
 };
 
-__host__ __device__ inline size_t round_smem_bytes(int R) { return (size_t)2 * KI * 8 + (size_t)2 * R * 8 + (size_t)R * 4; }
+// per warp, rounded to 16 bytes so that every warp's 8-byte arrays stay aligned for any degree R
+__host__ __device__ inline size_t round_smem_bytes(int R) {
+    return ((size_t)2 * KI * 8 + (size_t)2 * R * 8 + (size_t)R * 4 + 15) & ~(size_t)15;
+}
 
 template <int DT, int CPL>
 __global__ void __launch_bounds__(128) round_kernel(DoublingRound d) {

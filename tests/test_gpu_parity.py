@@ -365,3 +365,23 @@ def test_greedy_levels_at_every_row_width(rr, d):
             assert sum(len(x) for x in o_ids) > 40 * 8  # phase 2 runs
             assert_same(res, o_ids, o_d, len(Q))
         gi.close()
+
+
+def test_degree_not_multiple_of_four(rr):
+    """An odd degree (rows of 7 entries, 28 bytes): the per-warp shared-memory slices of the beam and
+    doubling kernels hold R-sized arrays and must stay 8-byte aligned for every warp (a slice of
+    2*KI*8 + 2*R*8 + R*4 bytes was not, and faulted); every variant gives the oracle's results."""
+    rng = np.random.default_rng(77)
+    n, d = 2000, 32
+    C = rng.integers(0, 256, size=(5, d))
+    X = np.clip(C[rng.integers(0, 5, n)] + rng.integers(-20, 21, size=(n, d)), 0, 255).astype(np.uint8)
+    Q = np.clip(C[rng.integers(0, 5, 50)] + rng.integers(-20, 21, size=(50, d)), 0, 255).astype(np.uint8)
+    d2 = ((X[None].astype(np.int64) - Q[:, None].astype(np.int64)) ** 2).sum(-1)
+    r = float(np.percentile(d2, 3))
+    adj, start = rrsynth.build_graph(X, 7, 24, 1.2, seed=7)
+    gi, oi = _tiny_index(rr, X, adj, start)
+    for v in VARS:
+        for b in (8, 32):
+            o_ids, o_d, _ = oracle.range_search(oi, Q, r, v, beam=b)
+            assert_same(gi.range_search(Q, r, v, beam=b), o_ids, o_d, len(Q))
+    gi.close()
