@@ -149,7 +149,7 @@ def peaks():
 
 # The form the GPU arm selects at AP >= 0.95 on each workload (from its own sweep); the reference arm, which
 # runs no sweep, times the oracle on that form.
-REF_FORM = {"c1": ("greedy", 192, 20, 1.0), "c3": ("greedy", 96, 20, 1.0), "c2": ("greedy_es", 8, 20, 1.0),
+REF_FORM = {"c1": ("greedy", 192, 20, 1.0), "c3": ("greedy_es", 96, 100, 2.0), "c2": ("greedy_es", 8, 20, 1.0),
             "c0": ("greedy", 64, 20, 1.0)}
 
 
