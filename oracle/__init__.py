@@ -141,7 +141,7 @@ def range_search_one(idx: Index, q, r, variant="greedy_es", beam=64, b_max=32768
 
 def range_search(idx: Index, Q, r, variant="greedy_es", beam=64, b_max=32768, es_vl=20, es_radius=None,
                  threads=1, es_metric="visited", expand=1):
-    """Batch driver (Alg. 6's parallel for; threads=1 is the single-threaded judge).
+    """Batch driver (Alg. 6's parallel for; threads=1 is the single-threaded reference).
 
     r: scalar or per-query array.  es_radius None means esr = r per query.  es_metric: the early-stopping
     metric M of Alg. 4 -- "visited" (Alg. 5), "top1", "top10" (thresholds in distance units, es_radius) or

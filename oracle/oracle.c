@@ -1,7 +1,7 @@
 /*
  * oracle/oracle.c -- CPU ORACLE for range retrieval on a proximity graph.
  *
- * TEST INFRASTRUCTURE ONLY.  This is the plain, slow, obviously correct judge
+ * TEST INFRASTRUCTURE ONLY.  This is the plain, slow, obviously correct reference
  * that the CUDA library is compared against.  Only the tests, the smoke check
  * and the CPU-baseline leg of the benchmark may load it; the library never
  * does.  It shares no code with the CUDA path.
@@ -507,7 +507,7 @@ void or_distances(const or_index *I, const void *q, const uint32_t *ids, int64_t
 }
 
 /* Alg. 6's "parallel for q in Q": runs or_range_search_one over a batch with
- * nthreads OpenMP threads (1 = the single-threaded judge).  Results land in
+ * nthreads OpenMP threads (1 = the single-threaded reference).  Results land in
  * per-query malloc'd buffers handed back through out_ids/out_d (free with
  * or_free).  Returns 0, or -1 if any query failed. */
 int or_range_search_batch(const or_index *I, const void *Q, int64_t nq, const double *radii, const or_params *P,

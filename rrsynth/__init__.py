@@ -5,7 +5,7 @@ library's tests and benchmark.  It holds none of the range-search method's
 arithmetic: it draws vectors and queries, picks a radius from exact 1-NN
 distances (numpy), builds the proximity graph once (``vamana.c``), and writes
 the ``.rrx`` index file.  The range search itself lives in ``oracle/`` (CPU
-judge) and in ``paper_2502_13245_gb300`` (CUDA), which share no code.
+reference) and in ``paper_2502_13245_gb300`` (CUDA), which share no code.
 
 The paper's datasets (BIGANN, SSNPP, Text2Image, ... in Table "Descriptions of
 each dataset") are not available; the recipes below stand in for them with
