@@ -44,9 +44,10 @@ ES_GRID = [(20, 1.0), (50, 1.5), (100, 2.0)]
 AP_TARGET = 0.95
 MULTI_PARENT = (2, 4)
 # DRAM bytes (read + write) of one launch of the roofline's kernel from an ncu capture of the current kernel
-# on this workload, keyed by (workload, variant, b); cleared whenever the kernel changes (none is current:
-# the 10^7-point workload's kernels are captured on its 2M-point recipe, see profiles/)
-MEASURED_TRAFFIC = {}
+# on this workload, keyed by (workload, variant, b); cleared whenever the kernel changes.  The 10^7-point
+# entry: dram__bytes_read.sum + dram__bytes_write.sum (a one-pass metric set) of the beam kernel's launch
+# inside the timed range, breadth-first index, default launch shape (profiles/beam_kernel_c3_traffic.md)
+MEASURED_TRAFFIC = {("c3", "greedy_es", 96): 69627017984 + 63060480}
 
 
 def log(*a):
