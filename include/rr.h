@@ -271,7 +271,9 @@ rr_status rr_index_relabel(rr_index *index, int32_t order);
  *              in the metric's own units (squared L2, or negative inner product)
  *   variant    rr_variant; params may be NULL (defaults)
  *   result_on_device  1: result arrays in device memory (ordered on stream),
- *              0: host memory
+ *              0: host memory: one pinned block from a library-owned pool
+ *              (at most 4 blocks, each reused once its result is freed, held
+ *              until the process exits), or malloc'd arrays when none is free
  * Returns once the result sizes are known (one host synchronisation per
  * phase); the CSR is complete when the call returns for host results, and
  * when `stream` reaches this point for device results.  RR_EOVERFLOW keeps a
@@ -426,7 +428,8 @@ rr_status rr_result_to_host(const rr_result *result, rr_result *host);
  * rr_serve_cfg, rr_serve_stats_t, rr_build_info.  Needs no GPU. */
 void rr_abi_sizes(int64_t out[8]);
 
-/* Free the arrays of a result (host or device) and zero the struct. */
+/* Free the arrays of a result (host or device) and zero the struct; a pooled
+ * host block goes back to the pool.  The arrays must not be freed any other way. */
 rr_status rr_result_free(rr_result *result);
 
 /* Message of the calling thread's last failure ("" if none). */

@@ -103,6 +103,10 @@ struct rr_index {
 
 namespace rr {
 rr_index *index_worker_view(rr_index *parent);
+// host arrays of a result: one pinned block from a small reuse pool (offsets at its base), else mallocs
+bool host_result_arrays(rr_result *out, int64_t nq, int64_t total, bool stats);
+void *host_pool_take(size_t bytes);
+bool host_pool_give(void *p);
 }  // namespace rr
 
 namespace rr {

@@ -9,6 +9,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -362,12 +363,7 @@ rr_status rr_result_to_host(const rr_result *r, rr_result *h) {
     h->nq = nq;
     h->total = tot;
     h->dist_dtype = r->dist_dtype;
-    h->offsets = (int64_t *)malloc((size_t)(nq + 1) * 8);
-    h->ids = (uint32_t *)malloc((size_t)std::max<int64_t>(tot, 1) * 4);
-    h->dists = malloc((size_t)std::max<int64_t>(tot, 1) * 4);
-    h->flags = (uint8_t *)malloc((size_t)std::max<int64_t>(nq, 1));
-    if (r->stats) h->stats = (rr_query_stats *)malloc((size_t)std::max<int64_t>(nq, 1) * sizeof(rr_query_stats));
-    if (!h->offsets || !h->ids || !h->dists || !h->flags || (r->stats && !h->stats)) {
+    if (!rr::host_result_arrays(h, nq, tot, r->stats != nullptr)) {
         rr_result_free(h);
         set_error("rr_result_to_host: allocation failed");
         return RR_ENOMEM;
@@ -402,7 +398,7 @@ rr_status rr_result_free(rr_result *r) {
         if (r->dists) cudaFreeAsync(r->dists, st);
         if (r->flags) cudaFreeAsync(r->flags, st);
         if (r->stats) cudaFreeAsync(r->stats, st);
-    } else {
+    } else if (!rr::host_pool_give(r->offsets)) {  // one pooled block holds every array; else separate mallocs
         free(r->offsets); free(r->ids); free(r->dists); free(r->flags); free(r->stats);
     }
     memset(r, 0, sizeof *r);
@@ -412,6 +408,85 @@ rr_status rr_result_free(rr_result *r) {
 }  // extern "C"
 
 namespace rr {
+
+// Pinned host blocks for host results: a device -> host copy into pinned memory runs at the link's
+// speed, one into fresh pageable memory pays for faulting and pinning its pages on every call.  Blocks
+// are reused after rr_result_free; at most kHostPoolBlocks are kept (held until the process exits), and
+// a result that finds none free falls back to malloc.
+namespace {
+constexpr int kHostPoolBlocks = 4;
+struct HostBlock {
+    void *p;
+    size_t cap;
+    bool busy;
+};
+std::mutex g_host_mu;
+std::vector<HostBlock> g_host_pool;
+}  // namespace
+
+void *host_pool_take(size_t bytes) {
+    std::lock_guard<std::mutex> lock(g_host_mu);
+    int best = -1, idle = -1;
+    for (int i = 0; i < (int)g_host_pool.size(); i++) {
+        const HostBlock &b = g_host_pool[(size_t)i];
+        if (b.busy) continue;
+        if (b.cap >= bytes && (best < 0 || b.cap < g_host_pool[(size_t)best].cap)) best = i;
+        if (idle < 0 || b.cap > g_host_pool[(size_t)idle].cap) idle = i;
+    }
+    if (best >= 0) {
+        g_host_pool[(size_t)best].busy = true;
+        return g_host_pool[(size_t)best].p;
+    }
+    if (idle < 0 && (int)g_host_pool.size() >= kHostPoolBlocks) return nullptr;
+    // a new block (replacing the largest idle one, which is too small), with a quarter of headroom
+    const size_t cap = std::max<size_t>(bytes + bytes / 4, (size_t)1 << 20);
+    void *p = nullptr;
+    if (cudaHostAlloc(&p, cap, cudaHostAllocPortable) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (idle >= 0) {
+        cudaFreeHost(g_host_pool[(size_t)idle].p);
+        g_host_pool[(size_t)idle] = HostBlock{p, cap, true};
+    } else {
+        g_host_pool.push_back(HostBlock{p, cap, true});
+    }
+    return p;
+}
+
+bool host_pool_give(void *p) {
+    if (!p) return false;
+    std::lock_guard<std::mutex> lock(g_host_mu);
+    for (HostBlock &b : g_host_pool)
+        if (b.p == p) {
+            b.busy = false;
+            return true;
+        }
+    return false;
+}
+
+bool host_result_arrays(rr_result *out, int64_t nq, int64_t total, bool stats) {
+    const size_t t = (size_t)std::max<int64_t>(total, 1), q = (size_t)std::max<int64_t>(nq, 1);
+    auto up = [](size_t x) { return (x + 63) & ~(size_t)63; };
+    // offsets first (the block's base: rr_result_free returns the block through it)
+    const size_t o_st = up((size_t)(nq + 1) * 8), o_ids = o_st + up(stats ? q * sizeof(rr_query_stats) : 0);
+    const size_t o_d = o_ids + up(t * 4), o_f = o_d + up(t * 4), end = o_f + q;
+    if (uint8_t *b = (uint8_t *)host_pool_take(end)) {
+        out->offsets = (int64_t *)b;
+        out->stats = stats ? (rr_query_stats *)(b + o_st) : nullptr;
+        out->ids = (uint32_t *)(b + o_ids);
+        out->dists = b + o_d;
+        out->flags = b + o_f;
+        return true;
+    }
+    out->offsets = (int64_t *)malloc((size_t)(nq + 1) * 8);
+    out->ids = (uint32_t *)malloc(t * 4);
+    out->dists = malloc(t * 4);
+    out->flags = (uint8_t *)malloc(q);
+    out->stats = stats ? (rr_query_stats *)malloc(q * sizeof(rr_query_stats)) : nullptr;
+    return out->offsets && out->ids && out->dists && out->flags && (!stats || out->stats);
+}
+
 rr_index *index_worker_view(rr_index *p) {
     rr_index *v = new (std::nothrow) rr_index();
     if (!v) return nullptr;

@@ -235,13 +235,7 @@ rr_status deliver(Search &S, int64_t total, uint32_t *ids, void *dists, rr_resul
         S.owned.clear();
         return RR_OK;
     }
-    const size_t t = (size_t)std::max<int64_t>(total, 1);
-    out->offsets = (int64_t *)malloc((size_t)(nq + 1) * 8);
-    out->ids = (uint32_t *)malloc(t * 4);
-    out->dists = malloc(t * 4);
-    out->flags = (uint8_t *)malloc((size_t)std::max<int64_t>(nq, 1));
-    out->stats = S.a.stats ? (rr_query_stats *)malloc((size_t)std::max<int64_t>(nq, 1) * sizeof(rr_query_stats)) : nullptr;
-    if (!out->offsets || !out->ids || !out->dists || !out->flags || (S.a.stats && !out->stats)) {
+    if (!host_result_arrays(out, nq, total, S.a.stats != nullptr)) {
         rr_result_free(out);
         set_error("result: host allocation failed");
         return RR_ENOMEM;
