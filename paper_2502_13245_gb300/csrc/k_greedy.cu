@@ -19,7 +19,10 @@
 // a candidate list; the evaluate pass gives each candidate a lane group that
 // gathers its vector and the query's, and appends the in-range ones as items
 // of the next level.  The set of items is the same either way (the bitmap
-// admits each point once per query, whichever pair claims it first).
+// admits each point once per query, whichever pair claims it first).  Both
+// passes append with one list reservation per warp iteration, and the
+// per-query result counts are taken from the finished item list by a
+// run-length pass, so no pass does an atomic per appended entry.
 #include <algorithm>
 
 #include "rr_common.cuh"
