@@ -101,6 +101,29 @@ def test_relabeled_arrays_are_the_same_graph():
         assert np.array_equal(X2[i], ds.X[old_of[i]])
 
 
+def test_search_commutes_with_the_renaming_when_no_distances_tie():
+    """With every distance distinct (fp32 data), no step of Alg. 1-3 depends on ids, so the oracle's search
+    on the relabeled arrays returns the original search's results renamed, for every variant."""
+    rng = np.random.default_rng(11)
+    n, d = 1500, 12
+    X = rng.standard_normal((n, d)).astype(np.float32)
+    Q = rng.standard_normal((30, d)).astype(np.float32)
+    adj, start = rrsynth.build_graph((X * 20 + 128).clip(0, 255).astype(np.uint8), 12, 24, 1.2, seed=3)
+    d2 = ((Q[:, None, :].astype(np.float64) - X[None].astype(np.float64)) ** 2).sum(-1)
+    r = float(np.percentile(d2, 4))
+    old_of = bfs_levels(adj, start)
+    X2, A2, s2 = relabeled_arrays(X, adj, start, old_of)
+    o1 = oracle.Index(X, adj, start)
+    o2 = oracle.Index(X2, A2, s2)
+    for v in ("beam", "beam_es", "greedy", "greedy_es", "doubling", "doubling_es"):
+        ids1, d1, st1 = oracle.range_search(o1, Q, r, v, beam=8)
+        ids2, dd2, st2 = oracle.range_search(o2, Q, r, v, beam=8)
+        for i in range(len(Q)):
+            assert np.array_equal(ids1[i], old_of[ids2[i]].astype(ids1[i].dtype)), (v, i)
+            assert np.array_equal(d1[i], dd2[i]), (v, i)
+            assert st1[i]["visits_beam"] == st2[i]["visits_beam"], (v, i)
+
+
 # ------------------------------------------------------------------------------------------- GPU
 
 @pytest.fixture(scope="module")
