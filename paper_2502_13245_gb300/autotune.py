@@ -22,6 +22,17 @@ SEEN_LOG2 = (9, 10, 11)
 PERSISTENT = (0, 1)
 
 
+def choose(runs, default, margin=0.98):
+    """The setting to keep from interleaved re-timings `runs` ({setting: [ms, ...]}): the one with the
+    lowest median, unless it is not the default and does not beat the default's median by more than
+    1 - margin (single timings of a few-millisecond batch differ by more than the settings do)."""
+    med = {c: sorted(v)[len(v) // 2] for c, v in runs.items()}
+    best = min(runs, key=lambda c: med[c])
+    if best != default and default in med and med[best] > margin * med[default]:
+        best = default
+    return best, med
+
+
 def _key(info, variant, beam):
     return "n%d_d%d_R%d_dt%d_%s_b%d" % (info.n, info.d, info.R, info.dtype, variant, beam)
 
@@ -75,10 +86,7 @@ def tune(index, queries, radius, variant, beam, stream=None, reps=3, cache_path=
     for _ in range(3):
         for c in cands:
             runs[c].append(time_it(*c, reps))
-    med = {c: sorted(v)[len(v) // 2] for c, v in runs.items()}
-    best = min(cands, key=lambda c: med[c])
-    if best != default and med[best] > 0.98 * med[default]:
-        best = default
+    best, med = choose(runs, default)
     if log:
         log("tune %s b=%d: default %.3f ms, chosen tile=%d seen=2^%d persistent=%d %.3f ms (medians)" % (
             variant, beam, med[default], best[0], best[1], best[2], med[best]))

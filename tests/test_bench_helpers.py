@@ -37,3 +37,17 @@ def test_bench_ap_matches_definition():
         tk = b.csr_keys(_Res(truth).offsets, _Res(truth).ids, n)
         got = b.average_precision(tk, _Res(found), n)
         assert abs(got - oracle.average_precision(truth, found)) < 1e-12
+
+
+def test_autotuner_keeps_a_shape_only_on_a_clear_win():
+    from paper_2502_13245_gb300.autotune import choose
+    d, a, b = (4, 10, 0), (8, 10, 1), (2, 9, 0)
+    # a is 1% faster than the default in the median: noise, the default stays
+    assert choose({d: [10.0, 10.2, 9.9], a: [9.9, 9.95, 9.8]}, d)[0] == d
+    # a is 5% faster: kept
+    assert choose({d: [10.0, 10.2, 9.9], a: [9.5, 9.4, 9.6]}, d)[0] == a
+    # the fastest by median wins among non-defaults, an outlier run does not decide
+    best, med = choose({d: [10.0, 10.0, 10.0], a: [9.0, 30.0, 9.1], b: [9.3, 9.2, 9.4]}, d)
+    assert best == a and med[a] == 9.1
+    # the default itself can win
+    assert choose({d: [8.0, 8.1, 8.2], a: [9.0, 9.0, 9.0]}, d)[0] == d
